@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the population annealing anneal step on GB300.
+
+A *step* is one temperature of the anneal (Sec. II.B): resampling from
+beta_{k-1} to beta_k (weights, prefix, multinomial draws, parents), the
+replica gather, N_S = 10 checkerboard Metropolis sweeps over all R replicas
+with energies, and the observables reduction.  Workload (default): 3D
+Edwards-Anderson +-J, L = 16 (N = 4096), R = 10^6 replicas bit-packed 64 per
+word (2 x 512 MB of state, larger than L2), 301 temperatures linear in beta
+from 0 to 5, synthetic seeded couplings.  W warm-up steps run first; the next
+K steps are timed with CUDA events on the library's stream.
+
+Metric: spin-flip attempts per ns (N R N_S attempts per step).  The JSON line
+also carries the sweep kernel's roofline (0.25 algorithmic bytes per attempt:
+one spin bit read and written per attempted flip), the oracle timed on the
+host cores, an end-to-end number through the C ABI from host buffers, the
+clocks seen during the timed region and the kernel launch count.
+
+--impl reference times the CPU oracle (the plain C implementation that the
+parity tests compare against) on a bounded sample of the same workload.
+Multi-GPU (torchrun): one independent instance per rank, no collective on the
+data path; value = all ranks' attempts / max-over-ranks time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin-flip attempts/ns on 1 GB300 (% HBM roofline); batched vs plain speedup"
+UNIT = "attempts/ns"
+BYTES_PER_ATTEMPT = 0.25  # per-sweep streaming: 1/8 byte read + 1/8 byte written per attempt
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        self.lines = []
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0])); smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _schedule(betas, n_needed):
+    if n_needed <= len(betas):
+        return betas
+    return np.concatenate([betas, np.full(n_needed - len(betas), betas[-1])])
+
+
+def _sweep_profile_traffic():
+    """dram bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "sweep_packed_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    src = open(os.path.join(ROOT, "paper_1710_09025_gb300", "csrc", "pa_packed.cu"), "rb").read()
+    if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return d.get("dram_bytes_per_full_launch")
+
+
+def oracle_rate(D, L, J, R_sample, betas, n_sweeps, seed, steps=None):
+    """Oracle attempts/ns on a bounded sample (single thread)."""
+    from oracle import oracle as O
+    O.build()
+    s = O.Sim(D, L, O.PM1, J, None, R_sample, betas, n_sweeps, seed)
+    N = L ** D
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(steps if steps is not None else len(betas)):
+        if s.step() < 0:
+            break
+        n += 1
+    dt = time.perf_counter() - t0
+    return n * N * R_sample * n_sweeps / (dt * 1e9), n, dt
+
+
+def run_reference(args, wl_name):
+    from paper_1710_09025_gb300 import workloads as Wk
+    w = Wk.WORKLOADS[wl_name]
+    J, _, betas = Wk.workload_inputs(wl_name)
+    D, L, ns = w["D"], w["L"], w["n_sweeps"]
+    R_s = 128
+    betas = _schedule(betas, args.warmup + args.steps)
+    from oracle import oracle as O
+    O.build()
+    s = O.Sim(D, L, O.PM1, J, None, R_s, betas, ns, w["seed"])
+    for _ in range(args.warmup):
+        s.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    dt = time.perf_counter() - t0
+    N = L ** D
+    v = args.steps * N * R_s * ns / (dt * 1e9)
+    sample = (f"oracle on {R_s} of the {w['R']} replicas (same lattice, couplings, schedule, N_S), "
+              f"steps k={args.warmup}..{args.warmup + args.steps - 1}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+            "data": "synthetic",
+            "config": {"workload": wl_name, "D": D, "L": L, "R": w["R"], "n_temps": len(betas),
+                       "n_sweeps": ns, "R_sample": R_s},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_gpu(args, wl_name):
+    import torch
+    import paper_1710_09025_gb300 as P
+    from paper_1710_09025_gb300 import workloads as Wk
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    P.load()
+    w = Wk.WORKLOADS[wl_name]
+    J, h, betas = Wk.workload_inputs(wl_name)
+    D, L, R, ns, kind = w["D"], w["L"], w["R"], w["n_sweeps"], w["kind"]
+    N = L ** D
+    betas = _schedule(betas, args.warmup + args.steps)
+    seed = w["seed"] + 1000 * rank
+    layout = {"packed": P.PA_LAYOUT_PACKED, "i8": P.PA_LAYOUT_I8}[w["layout"]]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pop = P.Population(D, L, kind, J, h, R, betas, ns, seed, layout=layout)
+    ctx = pop.ctx
+    P.pa_profile(ctx, True)
+    for _ in range(args.warmup):
+        P.pa_anneal_step(ctx)
+    P.pa_phase_times(ctx)  # discard warm-up timings
+    _, _, launches0 = P.pa_phase_times(ctx)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        P.pa_anneal_step(ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    phase_ms, phase_n, launches1 = P.pa_phase_times(ctx)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    attempts_step = N * R * ns
+    value = ws * args.steps * attempts_step / (ms * 1e6)
+    obs_last = P.pa_observables(ctx, args.warmup + args.steps - 1)
+    pop.close()
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peak, peak_kind = _peaks()
+    sweep_ms = phase_ms["sweep"] / max(phase_n["sweep"], 1)
+    bytes_launch = BYTES_PER_ATTEMPT * attempts_step
+    achieved = bytes_launch / (sweep_ms * 1e-3) / 1e9
+    traffic = _sweep_profile_traffic()
+    rs_ms = phase_ms["resample"] / max(phase_n["resample"], 1)
+    per_step = {k: phase_ms[k] / max(phase_n[k], 1) for k in ("resample", "gather", "sweep", "observe")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl_name, "D": D, "L": L, "N": N, "R": R, "n_temps": len(betas),
+                   "n_sweeps": ns, "layout": w["layout"], "couplings": "+-J" if kind == 0 else "gaussian",
+                   "schedule": "linear in beta, 0..%g" % w["beta_max"],
+                   "timed_k": [args.warmup, args.warmup + args.steps - 1],
+                   "l2": "state 2 x %.0f MB > 129 MB L2 (no flush needed)" % (8 * N * ((R + 63) // 64) / 1e6),
+                   "parallelism": "one independent instance per GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "sweep_packed_kernel",
+                     "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "note": "0.25 B per attempted flip (spin bit read + written per sweep); the "
+                             "kernel keeps the state in shared memory for all N_S sweeps and is "
+                             "bound by integer ALU (Philox), see alu_note"},
+        "phases_ms_per_step": per_step,
+        "sweep_attempts_per_ns": attempts_step / (sweep_ms * 1e6),
+        "resampled_replicas_per_s": R / (rs_ms * 1e-3) if rs_ms > 0 else None,
+        "gpu_launches": int(launches1 - launches0),
+        "clocks": clocks,
+        "observables_last": {"k": args.warmup + args.steps - 1, "E_mean_per_spin": obs_last["E_mean"] / N,
+                             "betaF": obs_last["betaF"], "S_f": obs_last["S_f"]},
+    }
+    if not args.no_e2e and ws == 1:
+        line["e2e"] = e2e_run(P, args, D, L, kind, J, h, R, betas, ns, seed, layout)
+    if not args.no_cpu_baseline and ws == 1:
+        R_s = 1024
+        sb = np.array([0.0, 1.25, 2.5, 3.75, 5.0])
+        v, n, dt = oracle_rate(D, L, J, R_s, sb, ns, w["seed"])
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{wl_name} lattice and couplings, R'={R_s} replicas, "
+                                          f"beta in {list(sb)}, N_S={ns}: {n} steps in {dt:.1f} s"}
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    print(json.dumps(line))
+
+
+def e2e_run(P, args, D, L, kind, J, h, R, betas, ns, seed, layout):
+    """Same metric through the public API from host buffers: pa_create (couplings
+    and schedule copied from host), K steps each followed by pa_observables
+    (device -> host read of the step's results), pa_destroy."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    opts = P.pa_options_default(layout=layout)
+    ctx = P.pa_create(D, L, kind, J, h, R, betas, ns, seed + 7, opts, stream=0)
+    for k in range(args.steps):
+        P.pa_anneal_step(ctx)
+        P.pa_observables(ctx, k)
+    P.pa_destroy(ctx)
+    dt = time.perf_counter() - t0
+    N = L ** D
+    h2d = J.nbytes + betas.nbytes + (0 if h is None else h.nbytes)
+    return {"value": args.steps * N * R * ns / (dt * 1e9), "unit": UNIT,
+            "h2d_bytes_per_step": int(round(h2d / args.steps)), "d2h_bytes_per_step": 96,
+            "note": "wall clock incl. allocation, host->device couplings/schedule, per-step "
+                    "observables read-back; steps k=0..K-1"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ea3d_L16_pm_R1e6")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        ws, rank, _ = _dist()
+        if rank == 0:
+            run_reference(args, args.workload)
+        return
+    run_gpu(args, args.workload)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * pa.h -- C ABI of the GB300 population annealing library (libpamc.so).
+ *
+ * Population annealing Monte Carlo (PAMC) for the Edwards-Anderson spin
+ * glass, arXiv:1710.09025:
+ *   Hamiltonian            Sec. II.A, Eq. (1): H = -sum_<ij> J_ij S_i S_j
+ *                          (plus -sum_i h_i S_i, an addition for the field gradient)
+ *   anneal step            Sec. II.B: resample beta -> beta' with copy numbers of mean
+ *                          proportional to exp[-(beta'-beta) E_i], then N_S Metropolis sweeps
+ *   spin selection         Sec. III.A: checkerboard (parity-0 sites, then parity-1 sites)
+ *   free energy            Sec. II.B: free-energy perturbation, beta F_k = -N ln 2 - sum ln Q_l
+ *   family entropy         Sec. II.B, Eq. (2)-(3): S_f, rho_s = R / e^{S_f}
+ *   overlap                Sec. V.A: overlap histogram of uncorrelated replicas
+ *   observable averages    Sec. V.A, Eq. (9)
+ *
+ * Conventions common to all calls
+ *   - Lattice: D in {2,3}, even L >= 2, periodic, N = L^D sites; site index
+ *     i = x + L y + L^2 z.  Bond (d, i) joins i and i + e_d; couplings are
+ *     passed as J[d*N + i] (D*N floats), the field as h[i] (N floats).
+ *   - Pointers named host_* or documented "host" are host memory owned by the
+ *     caller; the library copies from/to them before returning.  All device
+ *     memory is owned by the context (or by the caller for the *_ws variant).
+ *   - Every call returns PA_OK (0) or a negative PA_E* status; nothing aborts
+ *     or throws across the ABI.  pa_last_error() gives a message.
+ *   - One context per CUDA stream / host thread; calls on one context are not
+ *     thread-safe.
+ *   - Results are bit-for-bit reproducible: every random number comes from a
+ *     counter-based Philox4x32-10 stream keyed by (seed, instance, tag) and
+ *     addressed by (temperature index, sweep, site, replica); every rounding
+ *     that feeds the trajectory is specified (see the library's design notes).
+ */
+#ifndef PAMC_GB300_PA_H
+#define PAMC_GB300_PA_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PA_OK = 0,
+    PA_EINVAL = -1,   /* invalid argument (message says which)                 */
+    PA_ENOMEM = -2,   /* device or host allocation failed / workspace too small */
+    PA_ECUDA = -3,    /* a CUDA call failed (message has the CUDA error)        */
+    PA_ETIMEOUT = -4, /* a bounded device wait gave up                           */
+    PA_EDONE = -5,    /* the schedule is finished                                */
+    PA_ESTATE = -6    /* call not valid in the current state                     */
+};
+
+enum { PA_PM1 = 0, /* J in {-1,+1}, no field */
+       PA_REAL = 1 /* FP32 couplings, optional FP32 field */ };
+
+enum { PA_LAYOUT_AUTO = 0,   /* PM1 -> packed, REAL -> int8                          */
+       PA_LAYOUT_PACKED = 1, /* PM1 only: 64 replicas per uint64 word, bit 1 = spin -1 */
+       PA_LAYOUT_I8 = 2 };   /* one int8 (+1/-1) per spin, rows of N padded to 16     */
+
+typedef struct {
+    int32_t layout;          /* PA_LAYOUT_*                                            */
+    int32_t accumulate_grad; /* 1: keep per-temperature <s_i s_j>, <s_i> counts (REAL) */
+    uint32_t rng_instance;   /* 24-bit instance id in the Philox counter               */
+    uint32_t rng_tag;        /* 4-bit tag: independent populations (overlap)           */
+    int32_t threads;         /* 0 = tuned default; else threads per block              */
+    int32_t groups_per_block;/* 0 = tuned default (packed layout)                      */
+} pa_options;
+
+/* Per-temperature observables (Sec. II.B, Eq. 2-3; Sec. V.A, Eq. 9). */
+typedef struct {
+    double E_mean;   /* (1/R) sum_r E_r after the N_S sweeps at beta_k             */
+    double E2_mean;  /* (1/R) sum_r E_r^2                                           */
+    double C;        /* specific heat beta_k^2 (E2_mean - E_mean^2) / N             */
+    double lnQ;      /* ln Q_k, Q_k = (1/R) sum_r exp[-(beta_k-beta_{k-1}) E_r]; 0 at k=0 */
+    double betaF;    /* beta_k F_k = -N ln 2 - sum_{l=1..k} ln Q_l                  */
+    double S_f;      /* family entropy -sum_f nu_f ln nu_f                           */
+    double rho_s;    /* R / exp(S_f)                                                 */
+    int64_t R;       /* population size                                              */
+} pa_obs;
+
+typedef struct pa_ctx pa_ctx;
+
+/* Fills *opt with the defaults (auto layout, no grad, instance 0, tag 0, tuned). */
+int pa_options_default(pa_options* opt);
+
+/*
+ * pa_create -- allocate a population of R replicas on the current CUDA device.
+ *   D, L      lattice (D in {2,3}, L even, 2 <= L <= 16 in 3D, <= 64 in 2D)
+ *   kind      PA_PM1 (J exactly +-1, h must be NULL or all zero) or PA_REAL
+ *             (|J|,|h| < 4096; magnitudes below 2^-73 are flushed to zero so
+ *             that energies are exact fixed-point integers at scale 2^-96)
+ *   J         host, D*N floats, J[d*N+i] couples i and i+e_d
+ *   h         host, N floats or NULL (PA_REAL only)
+ *   R         replicas, 1 <= R <= 2^26
+ *   betas     host, n_temps doubles, betas[0] == 0, non-decreasing, finite
+ *   n_sweeps  Metropolis sweeps per temperature (N_S >= 0)
+ *   seed      Philox key
+ *   opt       NULL for defaults
+ *   stream    cudaStream_t to run on (NULL = legacy default stream)
+ * J, h and betas are deep-copied; the caller may free them on return.
+ * Errors: PA_EINVAL (bad argument), PA_ENOMEM, PA_ECUDA.  *out is NULL on error.
+ */
+int pa_create(pa_ctx** out, int D, int L, int kind, const float* J, const float* h, int R,
+              const double* betas, int n_temps, int n_sweeps, uint64_t seed,
+              const pa_options* opt, void* stream);
+
+/* Device workspace in bytes that pa_create_ws needs for these sizes. */
+int pa_workspace_size(int D, int L, int kind, int R, int n_temps, const pa_options* opt,
+                      size_t* bytes);
+/* As pa_create, but all large device buffers are carved from a caller-owned
+ * device allocation `workspace` of at least pa_workspace_size() bytes (256-byte
+ * aligned).  The caller keeps it alive until pa_destroy. */
+int pa_create_ws(pa_ctx** out, int D, int L, int kind, const float* J, const float* h, int R,
+                 const double* betas, int n_temps, int n_sweeps, uint64_t seed,
+                 const pa_options* opt, void* stream, void* workspace, size_t workspace_bytes);
+
+/* One anneal step at temperature index k = pa_current_step(): resampling from
+ * beta_{k-1} (k > 0), N_S sweeps at beta_k, energies and observables.
+ * Asynchronous on the context's stream.  PA_EDONE after the last temperature. */
+int pa_anneal_step(pa_ctx* ctx);
+/* n_steps steps (-1: the rest of the schedule) captured once into a CUDA graph
+ * and replayed; identical results to repeated pa_anneal_step. */
+int pa_anneal(pa_ctx* ctx, int n_steps);
+int pa_current_step(const pa_ctx* ctx);
+int pa_synchronize(pa_ctx* ctx);
+
+/* Observables of a completed step k (synchronises). */
+int pa_observables(pa_ctx* ctx, int k, pa_obs* out);
+/* beta F_k for every completed k (host, n_temps doubles; unfinished k -> NaN). */
+int pa_free_energy(pa_ctx* ctx, double* host_betaF);
+
+/*
+ * pa_grad -- backward pass of the free-energy estimate.  For the function
+ *   f = sum_k gbar[k] * beta_k F_k
+ * returns df/dJ_b = sum_k gbar[k] (-beta_k c_b(k) / R) and
+ *         df/dh_i = sum_k gbar[k] (-beta_k m_i(k) / R),
+ * with c_b(k) = sum_r S_i S_{i+e_d} and m_i(k) = sum_r S_i the exact integer
+ * population sums after the sweeps at beta_k (d(beta F)/dJ = -beta <S_i S_j>,
+ * d(beta F)/dh = -beta <S_i>; from Eq. 1 and Z = sum exp(-beta H)).
+ * Needs accumulate_grad; gbar host n_temps doubles (entries for steps not yet
+ * run must be 0); dJ host D*N doubles, dh host N doubles (or NULL). FP64,
+ * summed over k in increasing order. */
+int pa_grad(pa_ctx* ctx, const double* gbar, double* dJ, double* dh);
+
+/* Histogram of the overlap sum_i S^a_i S^b_i between slot r of two contexts of
+ * the same lattice and R (Sec. V.A); hist host int64[N+1], index
+ * (N + sum_i S^a_i S^b_i) / 2. */
+int pa_overlap(pa_ctx* a, pa_ctx* b, int64_t* hist);
+
+/* Copies of the current state to host memory (synchronise). */
+int pa_get_spins(pa_ctx* ctx, int8_t* host_spins /* R*N, +1/-1, replica-major */);
+/* Replicas [r0, r0 + n) only (0 <= r0, r0 + n <= R): n*N bytes, +1/-1. */
+int pa_get_spins_range(pa_ctx* ctx, int r0, int n, int8_t* host_spins);
+int pa_get_energies(pa_ctx* ctx, int64_t* host_E /* PM1: R values; REAL: 2R (lo, hi) of E*2^96 */);
+int pa_get_parents(pa_ctx* ctx, int32_t* host_parent /* R: parent of slot j at the last resampling */);
+int pa_get_family(pa_ctx* ctx, int32_t* host_family /* R: initial ancestor of slot j */);
+/* Grad counts (accumulate_grad): cJ n_temps*D*N, ch n_temps*N int64, host. */
+int pa_get_grad_counts(pa_ctx* ctx, int64_t* host_cJ, int64_t* host_ch);
+int pa_sizes(const pa_ctx* ctx, int* D, int* L, int* N, int* R, int* n_temps, int* layout);
+
+/* Per-phase timing with CUDA events recorded on the context's stream around
+ * each phase of pa_anneal_step (off by default; not recorded inside pa_anneal
+ * graphs).  Phases: 0 init, 1 resampling (weights..parents), 2 replica gather,
+ * 3 sweeps (+ energies), 4 observables. */
+enum { PA_PHASE_INIT = 0, PA_PHASE_RESAMPLE, PA_PHASE_GATHER, PA_PHASE_SWEEP, PA_PHASE_OBSERVE,
+       PA_NPHASE };
+int pa_profile(pa_ctx* ctx, int enable);
+/* Synchronises; writes the summed milliseconds and the number of timed phase
+ * instances per phase since the previous call (host ms[PA_NPHASE], n[PA_NPHASE],
+ * either may be NULL), and *launches = kernels enqueued by this context so far. */
+int pa_phase_times(pa_ctx* ctx, double* ms, int64_t* n, int64_t* launches);
+
+const char* pa_last_error(const pa_ctx* ctx); /* NULL ctx: last pa_create failure */
+void pa_destroy(pa_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

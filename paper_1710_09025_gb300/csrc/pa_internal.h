@@ -1,0 +1,112 @@
+// pa_internal.h -- declarations shared by the CUDA translation units of libpamc.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace pa {
+
+// Per-temperature accumulators kept on the device (one per step k).
+struct StepAcc {
+    long long sumE, sumE2;     // +-J: exact integer sums over the population
+    double sumEd, sumE2d;      // real couplings: FP64 sums (fixed order)
+    long long emin_lo, emin_hi;// lowest energy as int128 (+-J: sign-extended int32)
+    double lnQ;                // ln Q_k (0 at k = 0)
+    double sum_lnQ;            // sum_{l <= k} ln Q_l (sequential in l)
+    double betaF;              // beta_k F_k = -N ln 2 - sum_lnQ
+    double S;                  // sum of resampling weights (relative to E_min)
+    double sum_clnc;           // sum over families of c ln c (family entropy)
+    long long pad;
+};
+static_assert(sizeof(StepAcc) == 96, "StepAcc layout");
+
+// ---------------- packed +-J path ----------------
+struct PackedSweepArgs {
+    uint64_t* S;             // [G][N] words, updated in place
+    const uint8_t* jneg;     // [N] bit k: coupling to neighbour k (-x,+x,-y,+y,-z,+z) negative
+    int32_t* E;              // [R] energies out
+    int G, R;
+    int k, n_sweeps;
+    uint32_t key0, key1, c3;
+    uint32_t thr[4];         // thresholds (low 32 bits) of classes dE = 4c, c = 1..3
+    uint32_t und;            // bit c: class c needs a random comparison (0 < thr < 2^32)
+    uint32_t always;         // bit c: class c always accepted (thr == 2^32)
+    // int8 storage of the same algorithm (layout I8): rows of NP bytes
+    int8_t* S8_in;           // non-null: read rows parent[r] from here (fused gather)
+    int8_t* S8_out;          // write rows here
+    const int32_t* parent;   // or null (identity)
+    int NP;
+};
+cudaError_t launch_sweep_packed(int D, int L, const PackedSweepArgs& a, int gpb, int threads,
+                                cudaStream_t st);
+bool packed_supported(int D, int L);
+void packed_default_shape(int D, int L, int* gpb, int* threads);
+cudaError_t launch_init_packed(uint64_t* S, int N, int G, uint32_t k0, uint32_t k1, uint32_t c3,
+                               cudaStream_t st);
+cudaError_t launch_gather_packed(const uint64_t* Sold, uint64_t* Snew, const int32_t* parent,
+                                 int N, int G, int R, cudaStream_t st);
+cudaError_t launch_unpack_packed(const uint64_t* S, int8_t* out, int N, int r0, int n, cudaStream_t st);
+cudaError_t launch_overlap_packed(const uint64_t* A, const uint64_t* B, int N, int R,
+                                  unsigned long long* hist, cudaStream_t st);
+
+// ---------------- int8 path ----------------
+struct RealSweepArgs {
+    const int8_t* Sin;       // rows of NP bytes (+1/-1)
+    int8_t* Sout;
+    const int32_t* parent;   // gather rows parent[r] (or null)
+    const float* J;          // [D*N] (flushed)
+    const float* h;          // [N] or null
+    const longlong2* Jfix;   // [D*N] J * 2^96 as int128 (lo, hi)
+    const longlong2* hfix;   // [N] or null
+    longlong2* E;            // [R] energies * 2^96 out
+    unsigned long long* cJ;  // [D*N] grad counts of this step (or null)
+    unsigned long long* ch;  // [N]
+    int R, NP;
+    int k, n_sweeps;
+    float beta;
+    uint32_t key0, key1, c3;
+};
+cudaError_t launch_sweep_real(int D, int L, const RealSweepArgs& a, int warps, int grid,
+                              cudaStream_t st);
+bool real_supported(int D, int L);
+cudaError_t launch_init_i8(int8_t* S, int N, int NP, int R, uint32_t k0, uint32_t k1, uint32_t c3,
+                           cudaStream_t st);
+cudaError_t launch_overlap_i8(const int8_t* A, const int8_t* B, int N, int NP, int R,
+                              unsigned long long* hist, cudaStream_t st);
+
+// ---------------- resampling and observables ----------------
+struct ResampleArgs {
+    int R, kind;                 // kind 0: E32, 1: E128
+    const int32_t* E32;
+    const longlong2* E128;
+    const StepAcc* prev;         // acc[k-1]: E_min, sum_lnQ
+    StepAcc* cur;                // acc[k]: lnQ, sum_lnQ, betaF, S
+    double* w;                   // [R] weights
+    double* P;                   // [R] local prefix, then P
+    double* tot;                 // [nchunks] chunk sums
+    double* T;                   // [nchunks + 1] chunk offsets
+    int32_t* counts;             // [R] copy numbers (zero on entry, zeroed again on exit)
+    int32_t* blocksum;           // [nblocks] scratch for the count scan
+    int32_t* parent;             // [R] out
+    const int32_t* fam_in;       // [R]
+    int32_t* fam_out;            // [R]
+    double dbeta, log_R, betaF0;
+    int k;
+    uint32_t key0, key1, c3;
+};
+constexpr int kChunk = 1024;     // fixed summation chunk of the weight prefix
+constexpr int kScanBlock = 4096; // elements per block of the copy-number scan
+cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st);
+
+struct ObsArgs {
+    int R, kind;
+    const int32_t* E32;
+    const longlong2* E128;
+    const int32_t* family;
+    StepAcc* cur;
+};
+cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st);
+cudaError_t launch_grad_backward(const unsigned long long* cJ, const unsigned long long* ch,
+                                 const double* gbar, const double* betas, int n_temps, int nJ,
+                                 int N, int R, double* dJ, double* dh, cudaStream_t st);
+
+}  // namespace pa

@@ -1,0 +1,315 @@
+// pa_resample.cu -- resampling, observables and the gradient backward pass.
+//
+// Resampling (Sec. II.B): when beta rises to beta', replica i gets on average
+// R w_i / S copies, w_i = exp[-(beta'-beta)(E_i - E_min)], S = sum_i w_i
+// (multinomial: R independent draws).  Free-energy perturbation: ln Q =
+// -(beta'-beta) E_min + ln S - ln R and beta F_k = -N ln 2 - sum_{l<=k} ln Q_l.
+//
+// Fixed order, so that the draws do not depend on the launch geometry:
+//   P_i = T_c + L_i, L_i the sequential inclusive sum of w inside chunk
+//   c = i / 1024, T_0 = 0, T_{c+1} = T_c + L_last(c); S = P_{R-1}.
+// Draw q (RES stream) picks the smallest i with u_q S < P_i (if u_q S == S
+// after rounding: the smallest i with P_i >= u_q S).  Copy numbers are exact
+// integer counts; their exclusive scan places the copies of replica i in
+// slots [C_i, C_i + n_i), so families stay contiguous (Sec. V.A).
+#include "pa_device.cuh"
+#include "pa_internal.h"
+
+namespace pa {
+
+__device__ __forceinline__ __int128 ll2_to_i128(longlong2 v)
+{
+    return ((__int128)v.y << 64) | (unsigned long long)v.x;
+}
+
+__device__ __forceinline__ double e_minus_min_to_double(const ResampleArgs& a, int i)
+{
+    if (a.kind == 0) return (double)(a.E32[i] - (int)a.prev->emin_lo);  // exact integer
+    __int128 emin = ((__int128)a.prev->emin_hi << 64) | (unsigned long long)a.prev->emin_lo;
+    return __dmul_rn(i128_to_double(ll2_to_i128(a.E128[i]) - emin), 0x1p-96);
+}
+
+// weights and chunk-local sequential prefix sums (one block per chunk)
+__global__ void __launch_bounds__(256) rs_weights_kernel(ResampleArgs a)
+{
+    __shared__ double wsh[kChunk];
+    const int c = blockIdx.x, i0 = c * kChunk;
+    const int n = min(kChunk, a.R - i0);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const double d = e_minus_min_to_double(a, i0 + t);
+        const double w = spec_exp64(-__dmul_rn(a.dbeta, d));
+        wsh[t] = w;
+        a.w[i0 + t] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = wsh[0];
+        for (int t = 1; t < n; ++t) {
+            acc = __dadd_rn(acc, wsh[t]);
+            wsh[t] = acc;
+        }
+        a.tot[c] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) a.P[i0 + t] = wsh[t];
+}
+
+// chunk offsets (sequential), S, ln Q, running free energy
+__global__ void rs_offsets_kernel(ResampleArgs a, int nchunks)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double T = 0.0;
+    for (int c = 0; c < nchunks; ++c) {
+        a.T[c] = T;
+        T = __dadd_rn(T, a.tot[c]);
+    }
+    a.T[nchunks] = T;
+    const double S = T;
+    double emin_d;
+    if (a.kind == 0) {
+        emin_d = (double)(int)a.prev->emin_lo;
+    } else {
+        __int128 emin = ((__int128)a.prev->emin_hi << 64) | (unsigned long long)a.prev->emin_lo;
+        emin_d = __dmul_rn(i128_to_double(emin), 0x1p-96);
+    }
+    const double lnQ = __dsub_rn(__dadd_rn(-__dmul_rn(a.dbeta, emin_d), log(S)), a.log_R);
+    const double sum = __dadd_rn(a.prev->sum_lnQ, lnQ);
+    a.cur->lnQ = lnQ;
+    a.cur->sum_lnQ = sum;
+    a.cur->betaF = __dsub_rn(a.betaF0, sum);
+    a.cur->S = S;
+}
+
+__global__ void rs_finalize_kernel(ResampleArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.R) return;
+    a.P[i] = __dadd_rn(a.T[i / kChunk], a.P[i]);
+}
+
+__global__ void rs_draws_kernel(ResampleArgs a, int nchunks)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.R) return;
+    const u32x4 o = philox((uint32_t)q, (uint32_t)a.k, 0u, a.c3, a.key0, a.key1);
+    const double S = a.T[nchunks];
+    const double x = __dmul_rn(uniform53(o.x, o.y), S);
+    const double* __restrict__ P = a.P;
+    int lo = 0, hi = a.R;
+    while (lo < hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (x < P[mid]) hi = mid; else lo = mid + 1;
+    }
+    if (lo == a.R) {
+        lo = 0; hi = a.R;
+        while (lo < hi) {
+            const int mid = lo + ((hi - lo) >> 1);
+            if (P[mid] >= x) hi = mid; else lo = mid + 1;
+        }
+        if (lo >= a.R) lo = a.R - 1;  // unreachable: x = u S <= S = P[R-1]
+    }
+    atomicAdd(&a.counts[lo], 1);
+}
+
+__global__ void __launch_bounds__(1024) rs_blocksum_kernel(const int32_t* counts, int R, int32_t* blocksum)
+{
+    __shared__ int ws[32];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    int s = 0;
+    for (int t = 0; t < kScanBlock / 1024; ++t) {
+        const int i = b * kScanBlock + t * 1024 + tid;
+        if (i < R) s += counts[i];
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    if ((tid & 31) == 0) ws[tid >> 5] = s;
+    __syncthreads();
+    if (tid < 32) {
+        int v = __reduce_add_sync(0xffffffffu, ws[tid]);
+        if (tid == 0) blocksum[b] = v;
+    }
+}
+
+__global__ void rs_scan_blocks_kernel(int32_t* blocksum, int nb)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int acc = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int v = blocksum[b];
+        blocksum[b] = acc;
+        acc += v;
+    }
+}
+
+// exclusive scan inside the block + block offset; write parents and families
+__global__ void __launch_bounds__(1024) rs_fill_kernel(ResampleArgs a)
+{
+    __shared__ int ws[32];
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int PER = kScanBlock / 1024;
+    const int i0 = b * kScanBlock + tid * PER;
+    int c[PER];
+    int s = 0;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        c[t] = (i0 + t < a.R) ? a.counts[i0 + t] : 0;
+        s += c[t];
+    }
+    int incl = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = ws[lane];
+        int inc = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += u;
+        }
+        ws[lane] = inc - v;  // exclusive warp offsets
+    }
+    __syncthreads();
+    int off = a.blocksum[b] + ws[warp] + (incl - s);
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        const int i = i0 + t;
+        if (i < a.R) {
+            const int f = a.fam_in[i];
+            for (int u = 0; u < c[t]; ++u) {
+                a.parent[off + u] = i;
+                a.fam_out[off + u] = f;
+            }
+            off += c[t];
+            a.counts[i] = 0;
+        }
+    }
+}
+
+cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
+{
+    const int nchunks = (a.R + kChunk - 1) / kChunk;
+    const int nb = (a.R + kScanBlock - 1) / kScanBlock;
+    rs_weights_kernel<<<nchunks, 256, 0, st>>>(a);
+    rs_offsets_kernel<<<1, 32, 0, st>>>(a, nchunks);
+    rs_finalize_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
+    rs_draws_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a, nchunks);
+    rs_blocksum_kernel<<<nb, 1024, 0, st>>>(a.counts, a.R, a.blocksum);
+    rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a.blocksum, nb);
+    rs_fill_kernel<<<nb, 1024, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------- observables (Sec. V.A, Eq. 9; Sec. II.B, Eq. 2) ----------------
+// One block, fixed assignment and reduction tree: deterministic sums.
+__global__ void __launch_bounds__(1024) observe_kernel(ObsArgs a)
+{
+    __shared__ long long s_ll[2][32];
+    __shared__ double s_d[3][32];
+    __shared__ __int128 s_min[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    long long se = 0, se2 = 0;
+    double sed = 0.0, se2d = 0.0, clnc = 0.0;
+    __int128 mn = (__int128)(((unsigned __int128)1 << 127) - 1);
+    for (int j = tid; j < a.R; j += 1024) {
+        if (a.kind == 0) {
+            const long long e = a.E32[j];
+            se += e;
+            se2 += e * e;
+            if ((__int128)e < mn) mn = e;
+        } else {
+            const longlong2 v = a.E128[j];
+            const __int128 e = ((__int128)v.y << 64) | (unsigned long long)v.x;
+            const double ed = __dmul_rn(i128_to_double(e), 0x1p-96);
+            sed = __dadd_rn(sed, ed);
+            se2d = __fma_rn(ed, ed, se2d);
+            if (e < mn) mn = e;
+        }
+        const int f = a.family[j];
+        if (j == 0 || a.family[j - 1] != f) {
+            int lo = j + 1, hi = a.R;  // first index with family > f
+            while (lo < hi) {
+                const int mid = lo + ((hi - lo) >> 1);
+                if (a.family[mid] > f) hi = mid; else lo = mid + 1;
+            }
+            const double c = (double)(lo - j);
+            clnc = __fma_rn(c, log(c), clnc);
+        }
+    }
+    // warp reductions in a fixed pattern
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        se += __shfl_down_sync(0xffffffffu, se, off);
+        se2 += __shfl_down_sync(0xffffffffu, se2, off);
+        sed = __dadd_rn(sed, __shfl_down_sync(0xffffffffu, sed, off));
+        se2d = __dadd_rn(se2d, __shfl_down_sync(0xffffffffu, se2d, off));
+        clnc = __dadd_rn(clnc, __shfl_down_sync(0xffffffffu, clnc, off));
+        const long long lo = __shfl_down_sync(0xffffffffu, (long long)(unsigned long long)mn, off);
+        const long long hi = __shfl_down_sync(0xffffffffu, (long long)(mn >> 64), off);
+        const __int128 o = ((__int128)hi << 64) | (unsigned long long)lo;
+        if (o < mn) mn = o;
+    }
+    if (lane == 0) {
+        s_ll[0][warp] = se; s_ll[1][warp] = se2;
+        s_d[0][warp] = sed; s_d[1][warp] = se2d; s_d[2][warp] = clnc;
+        s_min[warp] = mn;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long A = 0, B = 0;
+        double C = 0.0, Dd = 0.0, F = 0.0;
+        __int128 M = s_min[0];
+        for (int w = 0; w < 32; ++w) {
+            A += s_ll[0][w]; B += s_ll[1][w];
+            C = __dadd_rn(C, s_d[0][w]); Dd = __dadd_rn(Dd, s_d[1][w]); F = __dadd_rn(F, s_d[2][w]);
+            if (s_min[w] < M) M = s_min[w];
+        }
+        a.cur->sumE = A; a.cur->sumE2 = B;
+        a.cur->sumEd = C; a.cur->sumE2d = Dd;
+        a.cur->sum_clnc = F;
+        a.cur->emin_lo = (long long)(unsigned long long)M;
+        a.cur->emin_hi = (long long)(M >> 64);
+    }
+}
+
+cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st)
+{
+    observe_kernel<<<1, 1024, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------- backward pass of sum_k gbar_k beta_k F_k ----------------
+// d(beta F)/dJ_b = -beta <S_i S_j>, d(beta F)/dh_i = -beta <S_i> (from Eq. 1),
+// estimated with the exact population sums after the sweeps at beta_k.
+__global__ void grad_backward_kernel(const unsigned long long* cJ, const unsigned long long* ch,
+                                     const double* gbar, const double* betas, int n_temps, int nJ,
+                                     int N, int R, double* dJ, double* dh)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nJ + N) return;
+    const bool isJ = b < nJ;
+    const int idx = isJ ? b : b - nJ;
+    const int stride = isJ ? nJ : N;
+    const unsigned long long* c = isJ ? cJ : ch;
+    double acc = 0.0;
+    const double invR = (double)R;
+    for (int k = 0; k < n_temps; ++k) {
+        const double m = __ddiv_rn((double)(long long)c[(size_t)k * stride + idx], invR);
+        acc = __dadd_rn(acc, __dmul_rn(gbar[k], -__dmul_rn(betas[k], m)));
+    }
+    if (isJ) dJ[idx] = acc; else dh[idx] = acc;
+}
+
+cudaError_t launch_grad_backward(const unsigned long long* cJ, const unsigned long long* ch,
+                                 const double* gbar, const double* betas, int n_temps, int nJ,
+                                 int N, int R, double* dJ, double* dh, cudaStream_t st)
+{
+    const int n = nJ + N;
+    grad_backward_kernel<<<(n + 255) / 256, 256, 0, st>>>(cJ, ch, gbar, betas, n_temps, nJ, N, R, dJ, dh);
+    return cudaGetLastError();
+}
+
+}  // namespace pa
