@@ -186,6 +186,8 @@ def run_gpu(args, wl_name):
     w = Wk.WORKLOADS[wl_name]
     J, h, betas = Wk.workload_inputs(wl_name)
     D, L, R, ns, kind = w["D"], w["L"], w["R"], w["n_sweeps"], w["kind"]
+    if args.R > 0:
+        R = args.R
     N = L ** D
     betas = _schedule(betas, args.warmup + args.steps)
     seed = w["seed"] + 1000 * rank
@@ -305,12 +307,13 @@ def e2e_run(P, args, D, L, kind, J, h, R, betas, ns, seed, layout):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=298)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="ea3d_L16_pm_R1e6")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--R", type=int, default=0, help="population override (profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
