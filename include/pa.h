@@ -168,6 +168,37 @@ int pa_profile(pa_ctx* ctx, int enable);
  * either may be NULL), and *launches = kernels enqueued by this context so far. */
 int pa_phase_times(pa_ctx* ctx, double* ms, int64_t* n, int64_t* launches);
 
+/*
+ * pa_resample_static -- the resampling step of pa_anneal_step for a +-J
+ * population, for callers that cannot allocate device memory (code inside a
+ * CUDA graph being captured, allocator-less embedded runtimes, hosts whose
+ * memory manager owns every device byte).  The paper has no counterpart; it
+ * exists for those callers.  No cudaMalloc, cudaFree or allocating library
+ * call is made: the scratch (weights, prefix sums, copy numbers, families)
+ * lives in one file-scope device array of PA_STATIC_SCRATCH_BYTES, which every
+ * GPU that loads the library keeps until the process exits.
+ *   d_E        device, R int32 energies of the population at beta_prev
+ *   R          1 <= R <= PA_STATIC_MAX_R; larger R returns PA_EINVAL
+ *   beta_prev, beta_next   finite, beta_prev <= beta_next
+ *   k          temperature index of the step (selects the draw stream)
+ *   seed, rng_instance (< 2^24), rng_tag (< 16)   as in pa_create / pa_options
+ *   d_parent   device, R int32 out: slot j takes replica d_parent[j]
+ *   d_lnQ      device, 1 double out: ln Q of this step
+ *   stream     cudaStream_t (NULL = legacy default stream)
+ * Results equal what pa_anneal_step computes for the same energies and step.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (that device must be current); make that first call
+ * before any stream capture.  Every call shares the one array and keeps the
+ * last call's contents: calls whose kernels overlap on the GPU (two streams,
+ * two host threads) race and must be serialised by the caller.
+ * Errors: PA_EINVAL, PA_ECUDA; message in pa_last_error(NULL).
+ */
+#define PA_STATIC_MAX_R 65536
+#define PA_STATIC_SCRATCH_BYTES (2u * 1024u * 1024u)
+int pa_resample_static(const int32_t* d_E, int R, double beta_prev, double beta_next, int k,
+                       uint64_t seed, uint32_t rng_instance, uint32_t rng_tag,
+                       int32_t* d_parent, double* d_lnQ, void* stream);
+
 const char* pa_last_error(const pa_ctx* ctx); /* NULL ctx: last pa_create failure */
 void pa_destroy(pa_ctx* ctx);
 

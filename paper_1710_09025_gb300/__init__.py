@@ -85,6 +85,8 @@ def load(path: str | None = None):
             "pa_sizes": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]),
             "pa_profile": (i32, [vp, i32]),
             "pa_phase_times": (i32, [vp, vp, vp, vp]),
+            "pa_resample_static": (i32, [vp, i32, ctypes.c_double, ctypes.c_double, i32, u64,
+                                         ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp]),
             "pa_last_error": (ctypes.c_char_p, [vp]),
             "pa_destroy": (None, [vp]),
         }
@@ -272,6 +274,19 @@ def pa_phase_times(ctx):
     launches = ctypes.c_int64(0)
     _check(load().pa_phase_times(ctx, _ptr(ms), _ptr(n), ctypes.byref(launches)), ctx)
     return dict(zip(PHASES, ms)), dict(zip(PHASES, n)), launches.value
+
+
+PA_STATIC_MAX_R = 65536
+
+
+def pa_resample_static(d_E, R, beta_prev, beta_next, k, seed, rng_instance, rng_tag, d_parent,
+                       d_lnQ, stream=None):
+    """Resampling with library-owned static device scratch (no allocation).
+    Pointers are device addresses (ints); see include/pa.h."""
+    st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    _check(load().pa_resample_static(ctypes.c_void_p(d_E), R, beta_prev, beta_next, k, seed,
+                                     rng_instance, rng_tag, ctypes.c_void_p(d_parent),
+                                     ctypes.c_void_p(d_lnQ), st))
 
 
 def pa_last_error(ctx=None) -> str:

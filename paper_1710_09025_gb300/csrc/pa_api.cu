@@ -88,6 +88,8 @@ static void phase_end(pa_ctx* c, int phase, cudaEvent_t start)
 
 static thread_local std::string g_create_err;
 
+void pa::set_global_error(const char* msg) { g_create_err = msg ? msg : ""; }
+
 #define PA_CK(ctx, call)                                                                 \
     do {                                                                                 \
         cudaError_t e__ = (call);                                                        \

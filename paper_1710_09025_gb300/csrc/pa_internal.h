@@ -109,4 +109,7 @@ cudaError_t launch_grad_backward(const unsigned long long* cJ, const unsigned lo
                                  const double* gbar, const double* betas, int n_temps, int nJ,
                                  int N, int R, double* dJ, double* dh, cudaStream_t st);
 
+// message returned by pa_last_error(NULL) for calls without a context
+void set_global_error(const char* msg);
+
 }  // namespace pa
