@@ -55,6 +55,7 @@ struct pa_ctx {
     int8_t* tmp8;
     unsigned long long* hist;
     double *gbar_d, *dJ_d, *dh_d;
+    pa::ObsPartial* obspart;
     cudaGraphExec_t gexec;
     std::string err;
     // profiling: event pairs per phase, launch counter
@@ -128,7 +129,7 @@ struct Layout {
 enum {
     W_J, W_H, W_JNEG, W_JFIX, W_HFIX, W_BETAS, W_S0, W_S1, W_E32, W_E128, W_PARENT, W_FAM0, W_FAM1,
     W_COUNTS, W_BLOCKSUM, W_W, W_P, W_TOT, W_T, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
-    W_DH, W_COUNT
+    W_DH, W_OBSPART, W_COUNT
 };
 
 static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps, int acc_grad)
@@ -166,6 +167,7 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
     sz[W_GBAR] = acc_grad ? sizeof(double) * n_temps : 0;
     sz[W_DJ] = acc_grad ? sizeof(double) * D * N : 0;
     sz[W_DH] = acc_grad ? sizeof(double) * N : 0;
+    sz[W_OBSPART] = sizeof(pa::ObsPartial) * pa::kObsBlocks;
     Layout lay;
     size_t off = 0;
     for (int i = 0; i < W_COUNT; ++i) {
@@ -343,6 +345,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->gbar_d = c->acc_grad ? (double*)at(W_GBAR) : nullptr;
     c->dJ_d = c->acc_grad ? (double*)at(W_DJ) : nullptr;
     c->dh_d = c->acc_grad ? (double*)at(W_DH) : nullptr;
+    c->obspart = (pa::ObsPartial*)at(W_OBSPART);
 
     // couplings: sign masks (+-J), fixed-point copies (real)
     std::vector<uint8_t> jn(N, 0);
@@ -450,13 +453,6 @@ static int enqueue_step(pa_ctx* c)
         c->launches += 7;
         phase_end(c, PA_PHASE_RESAMPLE, ev);
         c->famcur ^= 1;
-        if (c->layout == PA_LAYOUT_PACKED) {
-            ev = phase_begin(c);
-            PA_CK(c, pa::launch_gather_packed(c->S[c->cur], c->S[c->cur ^ 1], c->parent, N, c->G, R, c->st));
-            c->launches += 1;
-            phase_end(c, PA_PHASE_GATHER, ev);
-            c->cur ^= 1;
-        }
     }
     ev = phase_begin(c);
     if (c->kind == PA_PM1) {
@@ -470,7 +466,28 @@ static int enqueue_step(pa_ctx* c)
             if (thr >= 4294967296ull) a.always |= 1u << cl;
             else if (thr > 0) a.und |= 1u << cl;
         }
+        for (int r = 0; r < 10; ++r) {
+            a.rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+            a.rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+        }
+        // class of an uphill lane by its unsatisfied-bond count n: dE = 4D - 4n
+        const int cls_n0 = c->D, cls_n1 = c->D - 1, cls_n2 = c->D - 2;  // dE / 4
+        for (int b = 0; b < 32; ++b) {
+            auto bit = [&](int cl) -> uint32_t {
+                if (cl < 1 || cl > 3) return 0u;
+                return ((a.thr[cl] >> (31 - b)) & 1u) ? 0xFFFFFFFFu : 0u;
+            };
+            a.v00[b] = bit(cls_n0);
+            a.v01[b] = bit(cls_n1);
+            a.v10[b] = bit(cls_n2);
+        }
         if (c->layout == PA_LAYOUT_PACKED) {
+            // k > 0: the replica gather is fused into the sweep's tile load
+            a.Sin = c->S[c->cur];
+            if (k > 0) {
+                a.parent = c->parent;
+                c->cur ^= 1;
+            }
             a.S = c->S[c->cur];
         } else {
             a.S8_in = c->S8[c->cur]; a.S8_out = c->S8[c->cur ^ 1];
@@ -495,9 +512,9 @@ static int enqueue_step(pa_ctx* c)
     ev = phase_begin(c);
     pa::ObsArgs oa;
     oa.R = R; oa.kind = c->kind == PA_PM1 ? 0 : 1; oa.E32 = c->E32; oa.E128 = c->E128;
-    oa.family = c->fam[c->famcur]; oa.cur = c->acc + k;
+    oa.family = c->fam[c->famcur]; oa.part = c->obspart; oa.cur = c->acc + k;
     PA_CK(c, pa::launch_observe(oa, c->st));
-    c->launches += 1;
+    c->launches += 2;
     phase_end(c, PA_PHASE_OBSERVE, ev);
     c->k_next = k + 1;
     return PA_OK;

@@ -70,6 +70,25 @@ PA_HD u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t 
     return {c0, c1, c2, c3};
 }
 
+// Philox4x32-10 with the ten round keys precomputed (rk[2r] = k0 + r W0,
+// rk[2r+1] = k1 + r W1); identical output to philox().
+__device__ __forceinline__ u32x4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           const uint32_t (&rk)[20])
+{
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo2 = 0xCD9E8D57u * c2, hi2 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi2 ^ c1 ^ rk[2 * rnd];
+        const uint32_t n2 = hi0 ^ c3 ^ rk[2 * rnd + 1];
+        c0 = n0;
+        c1 = lo2;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return {c0, c1, c2, c3};
+}
+
 // 53-bit uniform in [0, 1) from two 32-bit words
 PA_HD double uniform53(uint32_t a, uint32_t b)
 {

@@ -21,7 +21,9 @@ static_assert(sizeof(StepAcc) == 96, "StepAcc layout");
 
 // ---------------- packed +-J path ----------------
 struct PackedSweepArgs {
-    uint64_t* S;             // [G][N] words, updated in place
+    uint64_t* S;             // [G][N] words out
+    const uint64_t* Sin;     // [G][N] words in (== S when there is no resampling); with
+                             // parent != null, lane j of group g reads replica parent[64g+j]
     const uint8_t* jneg;     // [N] bit k: coupling to neighbour k (-x,+x,-y,+y,-z,+z) negative
     int32_t* E;              // [R] energies out
     int G, R;
@@ -30,6 +32,11 @@ struct PackedSweepArgs {
     uint32_t thr[4];         // thresholds (low 32 bits) of classes dE = 4c, c = 1..3
     uint32_t und;            // bit c: class c needs a random comparison (0 < thr < 2^32)
     uint32_t always;         // bit c: class c always accepted (thr == 2^32)
+    uint32_t rk[20];         // Philox round keys: rk[2r] = k0 + r W0, rk[2r+1] = k1 + r W1
+    // per plane b (bit 31-b of the thresholds) as 0 / ~0 masks, selected by the
+    // two low bits (b1 b0) of the unsatisfied-bond count n of an uphill lane:
+    // v00: n = 0, v01: n = 1, v10: n = 2
+    uint32_t v00[32], v01[32], v10[32];
     // int8 storage of the same algorithm (layout I8): rows of NP bytes
     int8_t* S8_in;           // non-null: read rows parent[r] from here (fused gather)
     int8_t* S8_out;          // write rows here
@@ -42,8 +49,6 @@ bool packed_supported(int D, int L);
 void packed_default_shape(int D, int L, int* gpb, int* threads);
 cudaError_t launch_init_packed(uint64_t* S, int N, int G, uint32_t k0, uint32_t k1, uint32_t c3,
                                cudaStream_t st);
-cudaError_t launch_gather_packed(const uint64_t* Sold, uint64_t* Snew, const int32_t* parent,
-                                 int N, int G, int R, cudaStream_t st);
 cudaError_t launch_unpack_packed(const uint64_t* S, int8_t* out, int N, int r0, int n, cudaStream_t st);
 cudaError_t launch_overlap_packed(const uint64_t* A, const uint64_t* B, int N, int R,
                                   unsigned long long* hist, cudaStream_t st);
@@ -97,11 +102,17 @@ constexpr int kChunk = 1024;     // fixed summation chunk of the weight prefix
 constexpr int kScanBlock = 4096; // elements per block of the copy-number scan
 cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st);
 
+struct ObsPartial {
+    long long sumE, sumE2, min_lo, min_hi;
+    double sumEd, sumE2d, clnc, pad;
+};
+constexpr int kObsBlocks = 64;   // fixed partition of the observables reduction
 struct ObsArgs {
     int R, kind;
     const int32_t* E32;
     const longlong2* E128;
     const int32_t* family;
+    ObsPartial* part;            // [kObsBlocks] scratch
     StepAcc* cur;
 };
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st);

@@ -38,11 +38,27 @@ __device__ __forceinline__ int site_parity(int i)
     return (x + y + z) & 1;
 }
 
+// One plane of the comparison r < thr for the undecided lanes U.  T (the
+// threshold's bit for each lane's class) is selected by the count bits:
+// n = 0 -> v00, n = 1 -> v01, n = 2 -> v10 (0 / ~0 masks of this plane).
+// A lane whose plane bit differs from T is decided: accepted if T = 1.
+__device__ __forceinline__ void plane_step(uint64_t pl, uint32_t v00, uint32_t v01, uint32_t v10,
+                                           uint64_t b0, uint64_t b1, uint64_t& U, uint64_t& acc)
+{
+    const uint64_t V00 = (uint64_t)(int64_t)(int32_t)v00;
+    const uint64_t V01 = (uint64_t)(int64_t)(int32_t)v01;
+    const uint64_t V10 = (uint64_t)(int64_t)(int32_t)v10;
+    const uint64_t inner = (b0 & V01) | (~b0 & V00);
+    const uint64_t T = (b1 & V10) | (~b1 & inner);
+    acc |= U & T & ~pl;
+    U &= ~(T ^ pl);
+}
+
 // bits needed to count up to v
 __host__ __device__ constexpr int bits_for(int v) { return v <= 0 ? 1 : 1 + bits_for(v >> 1); }
 
 template <int D, int L, int GPB, int THREADS, bool I8>
-__global__ void __launch_bounds__(THREADS) sweep_packed_kernel(PackedSweepArgs a)
+__global__ void __launch_bounds__(THREADS, 4) sweep_packed_kernel(PackedSweepArgs a)
 {
     using LT = Lat<D, L>;
     constexpr int N = LT::N, NH = LT::NH;
@@ -64,11 +80,38 @@ __global__ void __launch_bounds__(THREADS) sweep_packed_kernel(PackedSweepArgs a
 
     for (int t = tid; t < N; t += THREADS) sj[t] = a.jneg[t];
 
-    if (!I8) {
+    if (!I8 && !a.parent) {
         for (int t = tid; t < ng * N; t += THREADS) {
             int gl = t / N, i = t - gl * N;
-            uint64_t w = a.S[(size_t)(g0 + gl) * N + i];
+            uint64_t w = a.Sin[(size_t)(g0 + gl) * N + i];
             sm[(gl * 2 + site_parity<D, L>(i)) * NH + (i >> 1)] = w;
+        }
+    } else if (!I8) {
+        // fused resampling gather: lane j of group g takes the bit of replica
+        // parent[64g+j]; parents are non-decreasing, so the 64 sources of a word
+        // sit in one to a few neighbouring groups.  Each thread owns destination
+        // lanes `lane` and `lane+32`; two ballots assemble a word; the word of
+        // site base+t is kept by lane t and stored once per 32 sites.
+        constexpr int NCH = (N + 31) / 32;
+        for (int tup = warp; tup < ng * NCH; tup += NWARP) {
+            const int gl = tup / NCH, base = (tup - gl * NCH) * 32;
+            const int r0 = 64 * (g0 + gl) + lane, r1 = r0 + 32;
+            const int s0 = r0 < a.R ? a.parent[r0] : r0;
+            const int s1 = r1 < a.R ? a.parent[r1] : r1;
+            const uint64_t* p0 = a.Sin + (size_t)(s0 >> 6) * N + base;
+            const uint64_t* p1 = a.Sin + (size_t)(s1 >> 6) * N + base;
+            const int sb0 = s0 & 63, sb1 = s1 & 63;
+            const int cnt = min(32, N - base);
+            uint64_t mine = 0;
+#pragma unroll 4
+            for (int t = 0; t < cnt; ++t) {
+                const uint64_t w0 = __ldg(p0 + t), w1 = __ldg(p1 + t);
+                const uint32_t lo = __ballot_sync(0xffffffffu, (uint32_t)(w0 >> sb0) & 1u);
+                const uint32_t hi = __ballot_sync(0xffffffffu, (uint32_t)(w1 >> sb1) & 1u);
+                if (lane == t) mine = (uint64_t)lo | ((uint64_t)hi << 32);
+            }
+            const int i = base + lane;
+            if (lane < cnt) sm[(gl * 2 + site_parity<D, L>(i)) * NH + (i >> 1)] = mine;
         }
     } else {
         // int8 rows -> bit words: one ballot per site and 32-lane half
@@ -95,7 +138,6 @@ __global__ void __launch_bounds__(THREADS) sweep_packed_kernel(PackedSweepArgs a
     }
     __syncthreads();
 
-    const uint32_t t1 = a.thr[1], t2 = a.thr[2], t3 = a.thr[3];
     const uint64_t und1 = (a.und & 2u) ? ~0ull : 0ull, und2 = (a.und & 4u) ? ~0ull : 0ull,
                    und3 = (a.und & 8u) ? ~0ull : 0ull;
     const uint64_t alw1 = (a.always & 2u) ? ~0ull : 0ull, alw2 = (a.always & 4u) ? ~0ull : 0ull,
@@ -115,43 +157,39 @@ __global__ void __launch_bounds__(THREADS) sweep_packed_kernel(PackedSweepArgs a
 #pragma unroll
                 for (int kk = 0; kk < 2 * D; ++kk)
                     u[kk] = s ^ oth[nb.q[kk]] ^ (((jm >> kk) & 1u) ? ~0ull : 0ull);
-                uint64_t m1, m2, m3;
+                uint64_t m1, m2, m3, b0, b1;
                 if (D == 3) {
                     uint64_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
                     uint64_t s2 = u[3] ^ u[4] ^ u[5], c2 = maj3(u[3], u[4], u[5]);
-                    uint64_t b0 = s1 ^ s2, k0 = s1 & s2;
-                    uint64_t b1 = c1 ^ c2 ^ k0, b2 = maj3(c1, c2, k0);
+                    b0 = s1 ^ s2;
+                    uint64_t k0 = s1 & s2;
+                    b1 = c1 ^ c2 ^ k0;
+                    uint64_t b2 = maj3(c1, c2, k0);
                     m3 = ~b2 & ~b1 & ~b0;  // n = 0: dE = 12
                     m2 = ~b2 & ~b1 & b0;   // n = 1: dE = 8
                     m1 = ~b2 & b1 & ~b0;   // n = 2: dE = 4
                 } else {
                     uint64_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
-                    uint64_t b0 = s1 ^ u[3], k0 = s1 & u[3];
-                    uint64_t b1 = c1 ^ k0, b2 = c1 & k0;
+                    b0 = s1 ^ u[3];
+                    uint64_t k0 = s1 & u[3];
+                    b1 = c1 ^ k0;
+                    uint64_t b2 = c1 & k0;
                     m3 = 0;
                     m2 = ~b2 & ~b1 & ~b0;  // n = 0: dE = 8
                     m1 = ~b2 & ~b1 & b0;   // n = 1: dE = 4
                 }
                 uint64_t acc = ~(m1 | m2 | m3) | (m1 & alw1) | (m2 & alw2) | (m3 & alw3);
                 uint64_t U = (m1 & und1) | (m2 & und2) | (m3 & und3);
-                m1 &= U; m2 &= U; m3 &= U;
                 const uint32_t g = (uint32_t)(g0 + gl);
-#pragma unroll 1
-                for (int m = 0; m < 16 && U; ++m) {
-                    u32x4 o = philox((uint32_t)q, hs, 16u * g + (uint32_t)m, a.c3, a.key0, a.key1);
-                    const uint64_t pl0 = (uint64_t)o.x | ((uint64_t)o.y << 32);
-                    const uint64_t pl1 = (uint64_t)o.z | ((uint64_t)o.w << 32);
-                    const int bA = 31 - 2 * m, bB = 30 - 2 * m;
-                    uint64_t T = (m1 & (0ull - (uint64_t)((t1 >> bA) & 1u))) |
-                                 (m2 & (0ull - (uint64_t)((t2 >> bA) & 1u))) |
-                                 (m3 & (0ull - (uint64_t)((t3 >> bA) & 1u)));
-                    acc |= U & T & ~pl0;
-                    U &= ~(T ^ pl0);
-                    T = (m1 & (0ull - (uint64_t)((t1 >> bB) & 1u))) |
-                        (m2 & (0ull - (uint64_t)((t2 >> bB) & 1u))) |
-                        (m3 & (0ull - (uint64_t)((t3 >> bB) & 1u)));
-                    acc |= U & T & ~pl1;
-                    U &= ~(T ^ pl1);
+                // MSB-first comparison r < thr over the planes still needed
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    if (!U) break;
+                    const u32x4 o = philox_rk((uint32_t)q, hs, 16u * g + (uint32_t)m, a.c3, a.rk);
+                    plane_step((uint64_t)o.x | ((uint64_t)o.y << 32), a.v00[2 * m], a.v01[2 * m],
+                               a.v10[2 * m], b0, b1, U, acc);
+                    plane_step((uint64_t)o.z | ((uint64_t)o.w << 32), a.v00[2 * m + 1], a.v01[2 * m + 1],
+                               a.v10[2 * m + 1], b0, b1, U, acc);
                 }
                 cur[q] = s ^ acc;
             }
@@ -341,47 +379,6 @@ cudaError_t launch_init_packed(uint64_t* S, int N, int G, uint32_t k0, uint32_t 
 {
     size_t n = (size_t)N * G;
     init_packed_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, N, G, k0, k1, c3);
-    return cudaGetLastError();
-}
-
-// Resampling gather (Sec. II.B): lane j of group g takes the bit of replica
-// parent[64g+j].  Parents are non-decreasing, so the sources of one word lie
-// in one to a few neighbouring groups.  One warp per destination group; each
-// thread owns destination lanes `lane` and `lane+32`; ballots assemble words;
-// the word for site base+t is kept by lane t and stored coalesced.
-__global__ void __launch_bounds__(256) gather_packed_kernel(const uint64_t* __restrict__ Sold,
-                                                            uint64_t* __restrict__ Snew,
-                                                            const int32_t* __restrict__ parent,
-                                                            int N, int G, int R)
-{
-    const int lane = threadIdx.x & 31;
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (g >= G) return;
-    const int r0 = 64 * g + lane, r1 = r0 + 32;
-    const int s0 = r0 < R ? parent[r0] : r0;
-    const int s1 = r1 < R ? parent[r1] : r1;
-    const uint64_t* p0 = Sold + (size_t)(s0 >> 6) * N;
-    const uint64_t* p1 = Sold + (size_t)(s1 >> 6) * N;
-    const int b0 = s0 & 63, b1 = s1 & 63;
-    uint64_t* dst = Snew + (size_t)g * N;
-    for (int base = 0; base < N; base += 32) {
-        uint64_t mine = 0;
-        const int cnt = min(32, N - base);
-#pragma unroll 4
-        for (int t = 0; t < cnt; ++t) {
-            const uint64_t w0 = __ldg(p0 + base + t), w1 = __ldg(p1 + base + t);
-            const uint32_t lo = __ballot_sync(0xffffffffu, (w0 >> b0) & 1ull);
-            const uint32_t hi = __ballot_sync(0xffffffffu, (w1 >> b1) & 1ull);
-            if (lane == t) mine = (uint64_t)lo | ((uint64_t)hi << 32);
-        }
-        if (lane < cnt) dst[base + lane] = mine;
-    }
-}
-
-cudaError_t launch_gather_packed(const uint64_t* Sold, uint64_t* Snew, const int32_t* parent,
-                                 int N, int G, int R, cudaStream_t st)
-{
-    gather_packed_kernel<<<(G + 7) / 8, 256, 0, st>>>(Sold, Snew, parent, N, G, R);
     return cudaGetLastError();
 }
 

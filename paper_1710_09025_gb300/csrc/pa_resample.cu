@@ -204,17 +204,21 @@ cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
 }
 
 // ---------------- observables (Sec. V.A, Eq. 9; Sec. II.B, Eq. 2) ----------------
-// One block, fixed assignment and reduction tree: deterministic sums.
-__global__ void __launch_bounds__(1024) observe_kernel(ObsArgs a)
+// kObsBlocks blocks each reduce a contiguous slice of the population in a
+// fixed order; one block combines the partials in block order.  The result
+// does not depend on the GPU (the partition depends only on R).
+__global__ void __launch_bounds__(1024) observe_partial_kernel(ObsArgs a)
 {
     __shared__ long long s_ll[2][32];
     __shared__ double s_d[3][32];
     __shared__ __int128 s_min[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (a.R + kObsBlocks - 1) / kObsBlocks;
+    const int j0 = blockIdx.x * per, j1 = min(a.R, j0 + per);
     long long se = 0, se2 = 0;
     double sed = 0.0, se2d = 0.0, clnc = 0.0;
     __int128 mn = (__int128)(((unsigned __int128)1 << 127) - 1);
-    for (int j = tid; j < a.R; j += 1024) {
+    for (int j = j0 + tid; j < j1; j += 1024) {
         if (a.kind == 0) {
             const long long e = a.E32[j];
             se += e;
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(1024) observe_kernel(ObsArgs a)
         }
         const int f = a.family[j];
         if (j == 0 || a.family[j - 1] != f) {
-            int lo = j + 1, hi = a.R;  // first index with family > f
+            int lo = j + 1, hi = a.R;  // first index with family > f (families are sorted)
             while (lo < hi) {
                 const int mid = lo + ((hi - lo) >> 1);
                 if (a.family[mid] > f) hi = mid; else lo = mid + 1;
@@ -239,7 +243,6 @@ __global__ void __launch_bounds__(1024) observe_kernel(ObsArgs a)
             clnc = __fma_rn(c, log(c), clnc);
         }
     }
-    // warp reductions in a fixed pattern
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         se += __shfl_down_sync(0xffffffffu, se, off);
@@ -259,25 +262,45 @@ __global__ void __launch_bounds__(1024) observe_kernel(ObsArgs a)
     }
     __syncthreads();
     if (tid == 0) {
-        long long A = 0, B = 0;
-        double C = 0.0, Dd = 0.0, F = 0.0;
+        ObsPartial p;
+        p.sumE = 0; p.sumE2 = 0; p.sumEd = 0.0; p.sumE2d = 0.0; p.clnc = 0.0; p.pad = 0.0;
         __int128 M = s_min[0];
         for (int w = 0; w < 32; ++w) {
-            A += s_ll[0][w]; B += s_ll[1][w];
-            C = __dadd_rn(C, s_d[0][w]); Dd = __dadd_rn(Dd, s_d[1][w]); F = __dadd_rn(F, s_d[2][w]);
+            p.sumE += s_ll[0][w]; p.sumE2 += s_ll[1][w];
+            p.sumEd = __dadd_rn(p.sumEd, s_d[0][w]); p.sumE2d = __dadd_rn(p.sumE2d, s_d[1][w]);
+            p.clnc = __dadd_rn(p.clnc, s_d[2][w]);
             if (s_min[w] < M) M = s_min[w];
         }
-        a.cur->sumE = A; a.cur->sumE2 = B;
-        a.cur->sumEd = C; a.cur->sumE2d = Dd;
-        a.cur->sum_clnc = F;
-        a.cur->emin_lo = (long long)(unsigned long long)M;
-        a.cur->emin_hi = (long long)(M >> 64);
+        p.min_lo = (long long)(unsigned long long)M;
+        p.min_hi = (long long)(M >> 64);
+        a.part[blockIdx.x] = p;
     }
+}
+
+__global__ void observe_final_kernel(ObsArgs a)
+{
+    if (threadIdx.x != 0) return;
+    long long A = 0, B = 0;
+    double C = 0.0, Dd = 0.0, F = 0.0;
+    __int128 M = (__int128)(((unsigned __int128)1 << 127) - 1);
+    for (int b = 0; b < kObsBlocks; ++b) {
+        const ObsPartial p = a.part[b];
+        A += p.sumE; B += p.sumE2;
+        C = __dadd_rn(C, p.sumEd); Dd = __dadd_rn(Dd, p.sumE2d); F = __dadd_rn(F, p.clnc);
+        const __int128 m = ((__int128)p.min_hi << 64) | (unsigned long long)p.min_lo;
+        if (m < M) M = m;
+    }
+    a.cur->sumE = A; a.cur->sumE2 = B;
+    a.cur->sumEd = C; a.cur->sumE2d = Dd;
+    a.cur->sum_clnc = F;
+    a.cur->emin_lo = (long long)(unsigned long long)M;
+    a.cur->emin_hi = (long long)(M >> 64);
 }
 
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st)
 {
-    observe_kernel<<<1, 1024, 0, st>>>(a);
+    observe_partial_kernel<<<kObsBlocks, 1024, 0, st>>>(a);
+    observe_final_kernel<<<1, 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
