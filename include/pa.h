@@ -168,6 +168,42 @@ int pa_profile(pa_ctx* ctx, int enable);
  * either may be NULL), and *launches = kernels enqueued by this context so far. */
 int pa_phase_times(pa_ctx* ctx, double* ms, int64_t* n, int64_t* launches);
 
+/* ---------------- batched instances ----------------
+ * Many disorder realisations annealed together: one persistent sweep launch
+ * covers every instance's replica tiles (mixed L, +-J and real couplings),
+ * resampling and observables run as one launch each for all instances, and
+ * pa_batch_run captures the schedule into a CUDA graph.  All instances share
+ * D, the schedule (betas, n_sweeps) and the Philox key (seed); each has its
+ * own rng_instance, so its results are identical to a single-instance
+ * context created with the same arguments.  Sweep shapes (groups per block of
+ * the packed tiles, persistent grid size) are chosen by timing candidates on
+ * the first step with k >= 1; every candidate gives bit-identical results. */
+typedef struct {
+    int L, kind;              /* lattice size, PA_PM1 or PA_REAL                    */
+    const float* J;           /* host, D*N                                          */
+    const float* h;           /* host, N or NULL                                    */
+    int R;                    /* replicas                                           */
+    uint32_t rng_instance;    /* < 2^24, distinct per instance                      */
+} pa_inst_desc;
+typedef struct pa_batch pa_batch;
+/* opt: layout must be AUTO; accumulate_grad must be 0; threads = 0 tunes the
+ * sweep shapes, threads = -1 keeps the defaults.  Errors as pa_create. */
+int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_desc* descs,
+                    const double* betas, int n_temps, int n_sweeps, uint64_t seed,
+                    const pa_options* opt, void* stream);
+int pa_batch_step(pa_batch* b);               /* one temperature for every instance       */
+int pa_batch_run(pa_batch* b, int n_steps);   /* n_steps (-1: the rest), graph-captured   */
+int pa_batch_current_step(const pa_batch* b);
+/* the context of instance i (owned by the batch: do not destroy); all getters
+ * (pa_observables, pa_get_spins, ...) work on it, and pa_anneal_step on it runs
+ * the same step with per-instance launches instead of the batched ones. */
+int pa_batch_instance(pa_batch* b, int i, pa_ctx** out);
+/* chosen sweep configuration: persistent blocks, packed groups-per-block
+ * multiplier (1 or 2), and the tuned sweep time of one step in ms */
+int pa_batch_sweep_config(const pa_batch* b, int* blocks, int* gpb_mult, double* ms);
+const char* pa_batch_last_error(const pa_batch* b);  /* NULL: last pa_batch_create failure */
+void pa_batch_destroy(pa_batch* b);
+
 /*
  * pa_resample_static -- the resampling step of pa_anneal_step for a +-J
  * population, for callers that cannot allocate device memory (code inside a

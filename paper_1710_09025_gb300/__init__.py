@@ -41,6 +41,11 @@ class pa_options(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("groups_per_block", ctypes.c_int32)]
 
 
+class pa_inst_desc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("kind", ctypes.c_int32), ("J", ctypes.c_void_p),
+                ("h", ctypes.c_void_p), ("R", ctypes.c_int32), ("rng_instance", ctypes.c_uint32)]
+
+
 class pa_obs(ctypes.Structure):
     _fields_ = [("E_mean", ctypes.c_double), ("E2_mean", ctypes.c_double), ("C", ctypes.c_double),
                 ("lnQ", ctypes.c_double), ("betaF", ctypes.c_double), ("S_f", ctypes.c_double),
@@ -87,6 +92,14 @@ def load(path: str | None = None):
             "pa_phase_times": (i32, [vp, vp, vp, vp]),
             "pa_resample_static": (i32, [vp, i32, ctypes.c_double, ctypes.c_double, i32, u64,
                                          ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp]),
+            "pa_batch_create": (i32, [P(vp), i32, i32, vp, vp, i32, i32, u64, P(pa_options), vp]),
+            "pa_batch_step": (i32, [vp]),
+            "pa_batch_run": (i32, [vp, i32]),
+            "pa_batch_current_step": (i32, [vp]),
+            "pa_batch_instance": (i32, [vp, i32, P(vp)]),
+            "pa_batch_sweep_config": (i32, [vp, P(i32), P(i32), P(ctypes.c_double)]),
+            "pa_batch_last_error": (ctypes.c_char_p, [vp]),
+            "pa_batch_destroy": (None, [vp]),
             "pa_last_error": (ctypes.c_char_p, [vp]),
             "pa_destroy": (None, [vp]),
         }
@@ -297,6 +310,67 @@ def pa_last_error(ctx=None) -> str:
 def pa_destroy(ctx):
     if ctx:
         load().pa_destroy(ctx)
+
+
+# ---------------- batched instances ----------------
+
+def _bcheck(rc, b=None):
+    if rc != PA_OK:
+        msg = load().pa_batch_last_error(b)
+        raise PAError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def pa_batch_create(D, instances, betas, n_sweeps, seed, options=None, stream=None):
+    """instances: list of dicts with L, kind, J, h (or None), R, rng_instance."""
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    keep = []
+    descs = (pa_inst_desc * len(instances))()
+    for d, inst in zip(descs, instances):
+        J = np.ascontiguousarray(inst["J"], dtype=np.float32)
+        h = None if inst.get("h") is None else np.ascontiguousarray(inst["h"], dtype=np.float32)
+        keep += [J, h]
+        d.L, d.kind, d.R, d.rng_instance = inst["L"], inst["kind"], inst["R"], inst["rng_instance"]
+        d.J = J.ctypes.data
+        d.h = None if h is None else h.ctypes.data
+    out = ctypes.c_void_p()
+    st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    _bcheck(load().pa_batch_create(ctypes.byref(out), D, len(instances), descs, _ptr(betas), len(betas),
+                                   n_sweeps, seed, ctypes.byref(options) if options else None, st))
+    return out
+
+
+def pa_batch_step(b):
+    rc = load().pa_batch_step(b)
+    if rc == PA_EDONE:
+        return False
+    _bcheck(rc, b)
+    return True
+
+
+def pa_batch_run(b, n_steps=-1):
+    _bcheck(load().pa_batch_run(b, n_steps), b)
+
+
+def pa_batch_current_step(b) -> int:
+    return load().pa_batch_current_step(b)
+
+
+def pa_batch_instance(b, i):
+    out = ctypes.c_void_p()
+    _bcheck(load().pa_batch_instance(b, i, ctypes.byref(out)), b)
+    return out
+
+
+def pa_batch_sweep_config(b):
+    blocks, mult, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _bcheck(load().pa_batch_sweep_config(b, ctypes.byref(blocks), ctypes.byref(mult), ctypes.byref(ms)), b)
+    return dict(blocks=blocks.value, gpb_mult=mult.value, tuned_ms=ms.value)
+
+
+def pa_batch_destroy(b):
+    if b:
+        load().pa_batch_destroy(b)
 
 
 class Population:

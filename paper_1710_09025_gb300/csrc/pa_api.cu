@@ -416,30 +416,60 @@ extern "C" int pa_create_ws(pa_ctx** out, int D, int L, int kind, const float* J
                        workspace, workspace_bytes);
 }
 
-// enqueue step k (no synchronisation)
-static int enqueue_step(pa_ctx* c)
+// Per-temperature parameters of the +-J sweep: Metropolis thresholds of the
+// uphill classes dE = 4c as plane masks, and the Philox round keys.
+static void fill_packed_step(pa::PackedStep* s, int D, double beta, int k, int n_sweeps,
+                             uint32_t k0, uint32_t k1)
+{
+    std::memset(s, 0, sizeof *s);
+    s->k = k;
+    s->n_sweeps = n_sweeps;
+    uint32_t thr[4] = {0, 0, 0, 0};
+    for (int cl = 1; cl <= 3; ++cl) {
+        const uint64_t t = pa::threshold_pm(beta, 4 * cl);
+        thr[cl] = (uint32_t)t;
+        if (t >= 4294967296ull) s->always |= 1u << cl;
+        else if (t > 0) s->und |= 1u << cl;
+    }
+    for (int r = 0; r < 10; ++r) {
+        s->rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        s->rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    // class of an uphill lane by its unsatisfied-bond count n: dE / 4 = D - n
+    const int cls_n0 = D, cls_n1 = D - 1, cls_n2 = D - 2;
+    for (int b = 0; b < 32; ++b) {
+        auto bit = [&](int cl) -> uint32_t {
+            if (cl < 1 || cl > 3) return 0u;
+            return ((thr[cl] >> (31 - b)) & 1u) ? 0xFFFFFFFFu : 0u;
+        };
+        s->v00[b] = bit(cls_n0);
+        s->v01[b] = bit(cls_n1);
+        s->v10[b] = bit(cls_n2);
+    }
+}
+
+// Everything one anneal step launches, with the context's ping-pong state
+// advanced to after the step.
+struct StepPlan {
+    int k;
+    pa::ResampleArgs rs;       // k > 0
+    pa::PackedSweepArgs pk;    // PA_PM1
+    pa::RealSweepArgs re;      // PA_REAL
+    pa::ObsArgs ob;
+    // context state after the step
+    int cur, famcur;
+};
+
+static void plan_step(pa_ctx* c, StepPlan* pl)
 {
     const int k = c->k_next;
-    if (k >= c->n_temps) { c->err = "schedule finished"; return PA_EDONE; }
     const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
-    const int N = c->N, R = c->R;
+    const int R = c->R;
     const double beta = c->betas[k];
-    cudaEvent_t ev;
-    if (k == 0) {
-        ev = phase_begin(c);
-        const uint32_t c3 = pa::counter3(pa::STREAM_INIT, c->tag, c->inst);
-        if (c->layout == PA_LAYOUT_PACKED)
-            PA_CK(c, pa::launch_init_packed(c->S[c->cur], N, c->G, k0, k1, c3, c->st));
-        else
-            PA_CK(c, pa::launch_init_i8(c->S8[c->cur], N, c->NP, R, k0, k1, c3, c->st));
-        iota_kernel<<<(R + 255) / 256, 256, 0, c->st>>>(c->fam[c->famcur], c->parent, R);
-        acc0_kernel<<<1, 1, 0, c->st>>>(c->acc, c->betaF0, R);
-        PA_CK(c, cudaGetLastError());
-        c->launches += 3;
-        phase_end(c, PA_PHASE_INIT, ev);
-    } else {
-        ev = phase_begin(c);
-        pa::ResampleArgs ra;
+    std::memset(pl, 0, sizeof *pl);
+    pl->k = k;
+    if (k > 0) {
+        pa::ResampleArgs& ra = pl->rs;
         ra.R = R; ra.kind = c->kind == PA_PM1 ? 0 : 1;
         ra.E32 = c->E32; ra.E128 = c->E128;
         ra.prev = c->acc + (k - 1); ra.cur = c->acc + k;
@@ -449,74 +479,93 @@ static int enqueue_step(pa_ctx* c)
         ra.dbeta = c->betas[k] - c->betas[k - 1];
         ra.log_R = c->log_R; ra.betaF0 = c->betaF0; ra.k = k;
         ra.key0 = k0; ra.key1 = k1; ra.c3 = pa::counter3(pa::STREAM_RES, c->tag, c->inst);
-        PA_CK(c, pa::launch_resample(ra, c->st));
-        c->launches += 7;
-        phase_end(c, PA_PHASE_RESAMPLE, ev);
         c->famcur ^= 1;
     }
-    ev = phase_begin(c);
     if (c->kind == PA_PM1) {
-        pa::PackedSweepArgs a;
-        std::memset(&a, 0, sizeof a);
-        a.jneg = c->jneg; a.E = c->E32; a.G = c->G; a.R = R; a.k = k; a.n_sweeps = c->n_sweeps;
-        a.key0 = k0; a.key1 = k1; a.c3 = pa::counter3(pa::STREAM_PLANE, c->tag, c->inst);
-        for (int cl = 1; cl <= 3; ++cl) {
-            const uint64_t thr = pa::threshold_pm(beta, 4 * cl);
-            a.thr[cl] = (uint32_t)thr;
-            if (thr >= 4294967296ull) a.always |= 1u << cl;
-            else if (thr > 0) a.und |= 1u << cl;
-        }
-        for (int r = 0; r < 10; ++r) {
-            a.rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
-            a.rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
-        }
-        // class of an uphill lane by its unsatisfied-bond count n: dE = 4D - 4n
-        const int cls_n0 = c->D, cls_n1 = c->D - 1, cls_n2 = c->D - 2;  // dE / 4
-        for (int b = 0; b < 32; ++b) {
-            auto bit = [&](int cl) -> uint32_t {
-                if (cl < 1 || cl > 3) return 0u;
-                return ((a.thr[cl] >> (31 - b)) & 1u) ? 0xFFFFFFFFu : 0u;
-            };
-            a.v00[b] = bit(cls_n0);
-            a.v01[b] = bit(cls_n1);
-            a.v10[b] = bit(cls_n2);
-        }
+        fill_packed_step(&pl->pk.s, c->D, beta, k, c->n_sweeps, k0, k1);
+        pa::PackedInst& in = pl->pk.i;
+        in.jneg = c->jneg; in.E = c->E32; in.G = c->G; in.R = R; in.NP = c->NP;
+        in.c3 = pa::counter3(pa::STREAM_PLANE, c->tag, c->inst);
         if (c->layout == PA_LAYOUT_PACKED) {
             // k > 0: the replica gather is fused into the sweep's tile load
-            a.Sin = c->S[c->cur];
+            in.Sin = c->S[c->cur];
             if (k > 0) {
-                a.parent = c->parent;
+                in.parent = c->parent;
                 c->cur ^= 1;
             }
-            a.S = c->S[c->cur];
+            in.S = c->S[c->cur];
         } else {
-            a.S8_in = c->S8[c->cur]; a.S8_out = c->S8[c->cur ^ 1];
-            a.parent = k > 0 ? c->parent : nullptr; a.NP = c->NP;
+            in.S8_in = c->S8[c->cur]; in.S8_out = c->S8[c->cur ^ 1];
+            in.parent = k > 0 ? c->parent : nullptr;
             c->cur ^= 1;
         }
-        PA_CK(c, pa::launch_sweep_packed(c->D, c->L, a, c->gpb, c->threads, c->st));
     } else {
-        pa::RealSweepArgs a;
-        a.Sin = c->S8[c->cur]; a.Sout = c->S8[c->cur ^ 1];
-        a.parent = k > 0 ? c->parent : nullptr;
-        a.J = c->J; a.h = c->h; a.Jfix = c->Jfix; a.hfix = c->hfix; a.E = c->E128;
-        a.cJ = c->acc_grad ? c->cJ + (size_t)k * c->D * N : nullptr;
-        a.ch = c->acc_grad ? c->ch + (size_t)k * N : nullptr;
-        a.R = R; a.NP = c->NP; a.k = k; a.n_sweeps = c->n_sweeps; a.beta = (float)beta;
-        a.key0 = k0; a.key1 = k1; a.c3 = pa::counter3(pa::STREAM_WORD, c->tag, c->inst);
-        PA_CK(c, pa::launch_sweep_real(c->D, c->L, a, c->real_warps, 0, c->st));
+        pa::RealStep& st = pl->re.s;
+        st.k = k; st.n_sweeps = c->n_sweeps; st.beta = (float)beta; st.key0 = k0; st.key1 = k1;
+        pa::RealInst& in = pl->re.i;
+        in.Sin = c->S8[c->cur]; in.Sout = c->S8[c->cur ^ 1];
+        in.parent = k > 0 ? c->parent : nullptr;
+        in.J = c->J; in.h = c->h; in.Jfix = c->Jfix; in.hfix = c->hfix; in.E = c->E128;
+        in.cJ = c->acc_grad ? c->cJ + (size_t)k * c->D * c->N : nullptr;
+        in.ch = c->acc_grad ? c->ch + (size_t)k * c->N : nullptr;
+        in.R = R; in.NP = c->NP; in.c3 = pa::counter3(pa::STREAM_WORD, c->tag, c->inst);
         c->cur ^= 1;
     }
+    pa::ObsArgs& oa = pl->ob;
+    oa.R = R; oa.kind = c->kind == PA_PM1 ? 0 : 1; oa.E32 = c->E32; oa.E128 = c->E128;
+    oa.family = c->fam[c->famcur]; oa.part = c->obspart; oa.cur = c->acc + k;
+    c->k_next = k + 1;
+    pl->cur = c->cur;
+    pl->famcur = c->famcur;
+}
+
+// enqueue the k = 0 initialisation of one context
+static int enqueue_init(pa_ctx* c)
+{
+    const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
+    const uint32_t c3 = pa::counter3(pa::STREAM_INIT, c->tag, c->inst);
+    if (c->layout == PA_LAYOUT_PACKED)
+        PA_CK(c, pa::launch_init_packed(c->S[c->cur], c->N, c->G, k0, k1, c3, c->st));
+    else
+        PA_CK(c, pa::launch_init_i8(c->S8[c->cur], c->N, c->NP, c->R, k0, k1, c3, c->st));
+    iota_kernel<<<(c->R + 255) / 256, 256, 0, c->st>>>(c->fam[c->famcur], c->parent, c->R);
+    acc0_kernel<<<1, 1, 0, c->st>>>(c->acc, c->betaF0, c->R);
+    PA_CK(c, cudaGetLastError());
+    c->launches += 3;
+    return PA_OK;
+}
+
+// enqueue step k (no synchronisation)
+static int enqueue_step(pa_ctx* c)
+{
+    const int k = c->k_next;
+    if (k >= c->n_temps) { c->err = "schedule finished"; return PA_EDONE; }
+    cudaEvent_t ev;
+    if (k == 0) {
+        ev = phase_begin(c);
+        int rc = enqueue_init(c);
+        if (rc) return rc;
+        phase_end(c, PA_PHASE_INIT, ev);
+    }
+    StepPlan pl;
+    plan_step(c, &pl);
+    if (k > 0) {
+        ev = phase_begin(c);
+        PA_CK(c, pa::launch_resample(pl.rs, c->st));
+        c->launches += 7;
+        phase_end(c, PA_PHASE_RESAMPLE, ev);
+    }
+    ev = phase_begin(c);
+    if (c->kind == PA_PM1)
+        PA_CK(c, pa::launch_sweep_packed(c->D, c->L, pl.pk, c->gpb, c->threads, c->st));
+    else
+        PA_CK(c, pa::launch_sweep_real(c->D, c->L, pl.re, c->real_warps, 0, c->st));
     c->launches += 1;
     phase_end(c, PA_PHASE_SWEEP, ev);
     ev = phase_begin(c);
-    pa::ObsArgs oa;
-    oa.R = R; oa.kind = c->kind == PA_PM1 ? 0 : 1; oa.E32 = c->E32; oa.E128 = c->E128;
-    oa.family = c->fam[c->famcur]; oa.part = c->obspart; oa.cur = c->acc + k;
-    PA_CK(c, pa::launch_observe(oa, c->st));
+    PA_CK(c, pa::launch_observe(pl.ob, c->st));
     c->launches += 2;
     phase_end(c, PA_PHASE_OBSERVE, ev);
-    c->k_next = k + 1;
     return PA_OK;
 }
 
@@ -778,3 +827,402 @@ extern "C" void pa_destroy(pa_ctx* c)
     if (c->own_ws) cudaFree(c->ws);
     delete c;
 }
+
+// ====================== batched instances ======================
+//
+// A batch owns one context per instance (carved from one workspace) plus
+// device tables with every instance's kernel arguments for every temperature
+// (built by plan_step, so the batched launches and the per-instance launches
+// follow the same ping-pong sequence).  A batched step is: k = 0 initialisation
+// per instance; resampling for all instances (one launch per kernel); one
+// persistent sweep launch over a work queue of (instance, tile) items; the
+// observables for all instances.
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+struct pa_batch {
+    int D, n_inst, n_temps, n_sweeps, k_next;
+    uint64_t seed;
+    cudaStream_t st;
+    void* ws;
+    std::vector<pa_ctx*> ctx;
+    std::vector<double> betas;
+    pa::ResampleArgs* d_rs;        // [n_temps][n_inst]
+    pa::BatchSweepInst* d_sw;      // [n_temps][n_inst]
+    pa::ObsArgs* d_ob;             // [n_temps][n_inst]
+    int2* d_items[2];              // work items per groups-per-block multiplier
+    int n_items[2];
+    size_t smem[2];
+    int* d_counters;               // [n_temps + kTuneSlots]
+    std::vector<int> after_cur, after_fam;  // [k * n_inst + i]: context state after step k
+    int maxR;
+    bool has_packed;
+    int tune_mode;                 // 0 tune, -1 defaults
+    bool tuned;
+    int blocks, mult, tune_slot;
+    double tuned_ms;
+    std::string sig;
+    cudaGraphExec_t gexec;
+    long long launches;
+    std::string err;
+};
+
+static constexpr int kTuneSlots = 64;
+static std::mutex g_tune_mu;
+static std::map<std::string, std::pair<int, int>> g_tune_cache;  // signature -> (blocks, mult)
+
+#define PB_CK(b, call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e__ = (call);                                                        \
+        if (e__ != cudaSuccess) {                                                        \
+            (b)->err = std::string(#call) + ": " + cudaGetErrorString(e__);              \
+            return PA_ECUDA;                                                             \
+        }                                                                                \
+    } while (0)
+
+static void batch_free(pa_batch* b)
+{
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (auto* c : b->ctx) pa_destroy(c);
+    cudaFree(b->d_rs);
+    cudaFree(b->d_sw);
+    cudaFree(b->d_ob);
+    cudaFree(b->d_items[0]);
+    cudaFree(b->d_items[1]);
+    cudaFree(b->d_counters);
+    cudaFree(b->ws);
+    delete b;
+}
+
+extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_desc* descs,
+                               const double* betas, int n_temps, int n_sweeps, uint64_t seed,
+                               const pa_options* opt, void* stream)
+{
+    if (!out) return PA_EINVAL;
+    *out = nullptr;
+    if (D != 3) { g_create_err = "batched sweeps support D = 3"; return PA_EINVAL; }
+    if (n_inst < 1 || !descs) { g_create_err = "need at least one instance"; return PA_EINVAL; }
+    if (opt && (opt->layout != PA_LAYOUT_AUTO || opt->accumulate_grad)) {
+        g_create_err = "batch: layout must be AUTO and accumulate_grad 0";
+        return PA_EINVAL;
+    }
+    pa_batch* b = new pa_batch();
+    b->D = D; b->n_inst = n_inst; b->n_temps = n_temps; b->n_sweeps = n_sweeps; b->k_next = 0;
+    b->seed = seed; b->st = (cudaStream_t)stream; b->ws = nullptr;
+    b->d_rs = nullptr; b->d_sw = nullptr; b->d_ob = nullptr;
+    b->d_items[0] = b->d_items[1] = nullptr; b->d_counters = nullptr; b->gexec = nullptr;
+    b->tune_mode = (opt && opt->threads < 0) ? -1 : 0;
+    b->tuned = b->tune_mode < 0;
+    b->blocks = 0; b->mult = 1; b->tune_slot = 0; b->tuned_ms = 0.0; b->launches = 0;
+    b->maxR = 0; b->has_packed = false;
+    // validate every instance and size the workspace
+    std::vector<size_t> offs(n_inst);
+    size_t total = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const pa_inst_desc& d = descs[i];
+        pa_options o;
+        pa_options_default(&o);
+        o.rng_instance = d.rng_instance;
+        std::string err;
+        int rc = validate(err, D, d.L, d.kind, d.J, d.h, d.R, betas, n_temps, n_sweeps, &o);
+        int cls, tiles;
+        size_t sm;
+        int G = (d.R + 63) / 64;
+        if (rc == PA_OK && !pa::batch_class(D, d.L, d.kind, 1, G, d.R, &cls, &tiles, &sm)) {
+            err = "lattice size not supported by the batched sweep (3D L in 4..12 even or 16)";
+            rc = PA_EINVAL;
+        }
+        if (rc) {
+            g_create_err = "instance " + std::to_string(i) + ": " + err;
+            delete b;
+            return rc;
+        }
+        int lay = resolve_layout(d.kind, &o);
+        offs[i] = total;
+        total += make_layout(D, d.L, d.kind, lay, d.R, n_temps, 0).total;
+        b->maxR = std::max(b->maxR, d.R);
+        b->has_packed |= d.kind == PA_PM1;
+    }
+    cudaError_t e = cudaMalloc(&b->ws, total);
+    if (e != cudaSuccess) {
+        g_create_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        delete b;
+        return PA_ENOMEM;
+    }
+    b->betas.assign(betas, betas + n_temps);
+    for (int i = 0; i < n_inst; ++i) {
+        const pa_inst_desc& d = descs[i];
+        pa_options o;
+        pa_options_default(&o);
+        o.rng_instance = d.rng_instance;
+        pa_ctx* c = nullptr;
+        size_t sz = make_layout(D, d.L, d.kind, resolve_layout(d.kind, &o), d.R, n_temps, 0).total;
+        int rc = create_impl(&c, D, d.L, d.kind, d.J, d.h, d.R, betas, n_temps, n_sweeps, seed, &o, stream,
+                             (char*)b->ws + offs[i], sz);
+        if (rc) {
+            g_create_err = "instance " + std::to_string(i) + ": " + g_create_err;
+            batch_free(b);
+            return rc;
+        }
+        b->ctx.push_back(c);
+    }
+    // argument tables for every (temperature, instance)
+    const size_t nt = (size_t)n_temps * n_inst;
+    std::vector<pa::ResampleArgs> rs(nt);
+    std::vector<pa::BatchSweepInst> sw(nt);
+    std::vector<pa::ObsArgs> ob(nt);
+    b->after_cur.resize(nt);
+    b->after_fam.resize(nt);
+    for (int i = 0; i < n_inst; ++i) {
+        pa_ctx* c = b->ctx[i];
+        int cls, tiles;
+        size_t sm;
+        pa::batch_class(D, c->L, c->kind, 1, c->G, c->R, &cls, &tiles, &sm);
+        for (int k = 0; k < n_temps; ++k) {
+            StepPlan pl;
+            plan_step(c, &pl);
+            const size_t at = (size_t)k * n_inst + i;
+            rs[at] = pl.rs;
+            std::memset(&sw[at], 0, sizeof sw[at]);
+            sw[at].cls = cls;
+            sw[at].pk = pl.pk.i;
+            sw[at].re = pl.re.i;
+            ob[at] = pl.ob;
+            b->after_cur[at] = pl.cur;
+            b->after_fam[at] = pl.famcur;
+        }
+        c->k_next = 0; c->cur = 0; c->famcur = 0;
+    }
+    // work items, most expensive first (estimated thread-instructions per tile)
+    for (int m = 1; m <= 2; ++m) {
+        struct It { double cost; int inst, tile; };
+        std::vector<It> items;
+        size_t smax = 0;
+        for (int i = 0; i < n_inst; ++i) {
+            pa_ctx* c = b->ctx[i];
+            int cls, tiles;
+            size_t sm;
+            pa::batch_class(D, c->L, c->kind, m, c->G, c->R, &cls, &tiles, &sm);
+            smax = std::max(smax, sm);
+            int gpb = 0, thr = 0;
+            pa::packed_default_shape(D, c->L, &gpb, &thr);
+            double cost = c->kind == PA_PM1 ? (double)gpb * m * c->N * 700.0 : 32.0 * c->N * 70.0;
+            for (int t = 0; t < tiles; ++t) items.push_back({cost, i, t});
+        }
+        std::stable_sort(items.begin(), items.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+        std::vector<int2> h(items.size());
+        for (size_t t = 0; t < items.size(); ++t) h[t] = make_int2(items[t].inst, items[t].tile);
+        b->n_items[m - 1] = (int)items.size();
+        b->smem[m - 1] = smax;
+        e = cudaMalloc(&b->d_items[m - 1], sizeof(int2) * h.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_items[m - 1], h.data(), sizeof(int2) * h.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_rs, sizeof(pa::ResampleArgs) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sw, sizeof(pa::BatchSweepInst) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ob, sizeof(pa::ObsArgs) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * (n_temps + kTuneSlots));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_rs, rs.data(), sizeof(pa::ResampleArgs) * nt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_sw, sw.data(), sizeof(pa::BatchSweepInst) * nt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_ob, ob.data(), sizeof(pa::ObsArgs) * nt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(int) * (n_temps + kTuneSlots));
+    if (e != cudaSuccess) {
+        g_create_err = std::string("batch tables: ") + cudaGetErrorString(e);
+        batch_free(b);
+        return PA_ECUDA;
+    }
+    // default sweep configuration: groups-per-block x1, as many blocks as fit
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (pa::batch_sweep_occupancy(std::max(b->smem[0], b->smem[1]), &per) != cudaSuccess || per < 1) per = 1;
+    b->blocks = sms * per;
+    // signature of the batch for the tuning cache: SM count and class histogram
+    std::map<std::pair<int, int>, int> hist;
+    for (auto* c : b->ctx) hist[{c->kind, c->L}] += 1;
+    b->sig = std::to_string(sms) + "|" + std::to_string(n_sweeps);
+    for (auto& kv : hist)
+        b->sig += "|" + std::to_string(kv.first.first) + ":" + std::to_string(kv.first.second) + "x" +
+                  std::to_string(kv.second);
+    if (b->tune_mode == 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(b->sig);
+        if (it != g_tune_cache.end()) {
+            b->blocks = it->second.first;
+            b->mult = it->second.second;
+            b->tuned = true;
+        }
+    }
+    *out = b;
+    return PA_OK;
+}
+
+static void batch_step_params(pa_batch* b, int k, pa::PackedStep* ps, pa::RealStep* rs)
+{
+    const uint32_t k0 = (uint32_t)b->seed, k1 = (uint32_t)(b->seed >> 32);
+    fill_packed_step(ps, b->D, b->betas[k], k, b->n_sweeps, k0, k1);
+    rs->k = k; rs->n_sweeps = b->n_sweeps; rs->beta = (float)b->betas[k]; rs->key0 = k0; rs->key1 = k1;
+}
+
+// time every candidate sweep configuration on step k; a sweep with k >= 1
+// reads its input replicas from one buffer and writes another, so re-running
+// it gives the same outputs, and every candidate gives identical results
+static int batch_tune(pa_batch* b, int k)
+{
+    pa::PackedStep ps;
+    pa::RealStep rs;
+    batch_step_params(b, k, &ps, &rs);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaEvent_t e0, e1;
+    PB_CK(b, cudaEventCreate(&e0));
+    PB_CK(b, cudaEventCreate(&e1));
+    double best = 1e30;
+    int bb = b->blocks, bm = 1;
+    const pa::BatchSweepInst* tab = b->d_sw + (size_t)k * b->n_inst;
+    for (int m = 1; m <= (b->has_packed ? 2 : 1); ++m) {
+        int per = 0;
+        if (pa::batch_sweep_occupancy(b->smem[m - 1], &per) != cudaSuccess || per < 1) continue;
+        for (int bps = 1; bps <= per; ++bps) {
+            if (b->tune_slot >= kTuneSlots) break;
+            int* ctr = b->d_counters + b->n_temps + b->tune_slot++;
+            PB_CK(b, cudaEventRecord(e0, b->st));
+            PB_CK(b, pa::launch_sweep_batched(ps, rs, tab, b->d_items[m - 1], b->n_items[m - 1], m, ctr,
+                                              sms * bps, b->smem[m - 1], b->st));
+            PB_CK(b, cudaEventRecord(e1, b->st));
+            PB_CK(b, cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; bb = sms * bps; bm = m; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->blocks = bb;
+    b->mult = bm;
+    b->tuned_ms = best;
+    b->tuned = true;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[b->sig] = {bb, bm};
+    return PA_OK;
+}
+
+static int batch_enqueue(pa_batch* b, bool allow_tune)
+{
+    const int k = b->k_next;
+    if (k >= b->n_temps) { b->err = "schedule finished"; return PA_EDONE; }
+    if (k == 0) {
+        for (auto* c : b->ctx) {
+            int rc = enqueue_init(c);
+            if (rc) { b->err = c->err; return rc; }
+            b->launches += 3;
+        }
+    } else {
+        PB_CK(b, pa::launch_resample_batched(b->d_rs + (size_t)k * b->n_inst, b->n_inst, b->maxR, b->st));
+        b->launches += 7;
+    }
+    if (!b->tuned && allow_tune && k >= 1) {
+        int rc = batch_tune(b, k);
+        if (rc) return rc;
+    }
+    pa::PackedStep ps;
+    pa::RealStep rs;
+    batch_step_params(b, k, &ps, &rs);
+    PB_CK(b, pa::launch_sweep_batched(ps, rs, b->d_sw + (size_t)k * b->n_inst, b->d_items[b->mult - 1],
+                                      b->n_items[b->mult - 1], b->mult, b->d_counters + k, b->blocks,
+                                      b->smem[b->mult - 1], b->st));
+    PB_CK(b, pa::launch_observe_batched(b->d_ob + (size_t)k * b->n_inst, b->n_inst, b->st));
+    b->launches += 3;
+    for (int i = 0; i < b->n_inst; ++i) {
+        pa_ctx* c = b->ctx[i];
+        c->k_next = k + 1;
+        c->cur = b->after_cur[(size_t)k * b->n_inst + i];
+        c->famcur = b->after_fam[(size_t)k * b->n_inst + i];
+    }
+    b->k_next = k + 1;
+    return PA_OK;
+}
+
+extern "C" int pa_batch_step(pa_batch* b)
+{
+    if (!b) return PA_EINVAL;
+    for (auto* c : b->ctx)
+        if (c->k_next != b->k_next) { b->err = "an instance was stepped on its own"; return PA_ESTATE; }
+    return batch_enqueue(b, true);
+}
+
+extern "C" int pa_batch_run(pa_batch* b, int n_steps)
+{
+    if (!b) return PA_EINVAL;
+    if (b->k_next >= b->n_temps) { b->err = "schedule finished"; return PA_EDONE; }
+    int n = n_steps < 0 ? b->n_temps - b->k_next : n_steps;
+    if (b->k_next + n > b->n_temps) { b->err = "n_steps past the end of the schedule"; return PA_EINVAL; }
+    // the first steps run eagerly: k = 0 initialises, the first k >= 1 tunes
+    while (n > 0 && (b->k_next == 0 || !b->tuned || !b->st)) {
+        int rc = pa_batch_step(b);
+        if (rc) return rc;
+        --n;
+    }
+    if (n == 0) return PA_OK;
+    if (b->gexec) {
+        PB_CK(b, cudaStreamSynchronize(b->st));
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    const int k_save = b->k_next;
+    const long long l_save = b->launches;
+    std::vector<int> st_save;
+    for (auto* c : b->ctx) { st_save.push_back(c->k_next); st_save.push_back(c->cur); st_save.push_back(c->famcur); }
+    PB_CK(b, cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    int rc = PA_OK;
+    for (int t = 0; t < n && rc == PA_OK; ++t) rc = batch_enqueue(b, false);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->st, &g);
+    if (rc == PA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (rc != PA_OK || e != cudaSuccess) {
+        b->k_next = k_save;
+        b->launches = l_save;
+        for (size_t i = 0; i < b->ctx.size(); ++i) {
+            b->ctx[i]->k_next = st_save[3 * i];
+            b->ctx[i]->cur = st_save[3 * i + 1];
+            b->ctx[i]->famcur = st_save[3 * i + 2];
+        }
+        b->gexec = nullptr;
+        if (rc == PA_OK) { b->err = std::string("batch graph: ") + cudaGetErrorString(e); rc = PA_ECUDA; }
+        return rc;
+    }
+    PB_CK(b, cudaGraphLaunch(b->gexec, b->st));
+    return PA_OK;
+}
+
+extern "C" int pa_batch_current_step(const pa_batch* b) { return b ? b->k_next : PA_EINVAL; }
+
+extern "C" int pa_batch_instance(pa_batch* b, int i, pa_ctx** out)
+{
+    if (!b || !out || i < 0 || i >= b->n_inst) return PA_EINVAL;
+    *out = b->ctx[i];
+    return PA_OK;
+}
+
+extern "C" int pa_batch_sweep_config(const pa_batch* b, int* blocks, int* gpb_mult, double* ms)
+{
+    if (!b) return PA_EINVAL;
+    if (blocks) *blocks = b->blocks;
+    if (gpb_mult) *gpb_mult = b->mult;
+    if (ms) *ms = b->tuned_ms;
+    return PA_OK;
+}
+
+extern "C" const char* pa_batch_last_error(const pa_batch* b)
+{
+    return b ? b->err.c_str() : g_create_err.c_str();
+}
+
+extern "C" void pa_batch_destroy(pa_batch* b) { batch_free(b); }

@@ -20,28 +20,33 @@ struct StepAcc {
 static_assert(sizeof(StepAcc) == 96, "StepAcc layout");
 
 // ---------------- packed +-J path ----------------
-struct PackedSweepArgs {
-    uint64_t* S;             // [G][N] words out
-    const uint64_t* Sin;     // [G][N] words in (== S when there is no resampling); with
-                             // parent != null, lane j of group g reads replica parent[64g+j]
-    const uint8_t* jneg;     // [N] bit k: coupling to neighbour k (-x,+x,-y,+y,-z,+z) negative
-    int32_t* E;              // [R] energies out
-    int G, R;
+// Parameters of one temperature, uniform over every instance of a launch.
+struct PackedStep {
     int k, n_sweeps;
-    uint32_t key0, key1, c3;
-    uint32_t thr[4];         // thresholds (low 32 bits) of classes dE = 4c, c = 1..3
-    uint32_t und;            // bit c: class c needs a random comparison (0 < thr < 2^32)
+    uint32_t und;            // bit c: class c (dE = 4c) needs a random comparison (0 < thr < 2^32)
     uint32_t always;         // bit c: class c always accepted (thr == 2^32)
     uint32_t rk[20];         // Philox round keys: rk[2r] = k0 + r W0, rk[2r+1] = k1 + r W1
     // per plane b (bit 31-b of the thresholds) as 0 / ~0 masks, selected by the
     // two low bits (b1 b0) of the unsatisfied-bond count n of an uphill lane:
     // v00: n = 0, v01: n = 1, v10: n = 2
     uint32_t v00[32], v01[32], v10[32];
-    // int8 storage of the same algorithm (layout I8): rows of NP bytes
-    int8_t* S8_in;           // non-null: read rows parent[r] from here (fused gather)
-    int8_t* S8_out;          // write rows here
+};
+// Parameters of one instance.
+struct PackedInst {
+    uint64_t* S;             // [G][N] words out
+    const uint64_t* Sin;     // [G][N] words in (== S without resampling); with parent != null,
+                             // lane j of group g reads replica parent[64g+j]
+    const uint8_t* jneg;     // [N] bit k: coupling to neighbour k (-x,+x,-y,+y,-z,+z) negative
+    int32_t* E;              // [R] energies out
+    int8_t* S8_in;           // int8 storage of the same algorithm (layout I8): rows of NP bytes
+    int8_t* S8_out;          // non-null selects the int8 storage
     const int32_t* parent;   // or null (identity)
-    int NP;
+    int G, R, NP;
+    uint32_t c3;             // Philox counter word 3 of the PLANE stream
+};
+struct PackedSweepArgs {
+    PackedStep s;
+    PackedInst i;
 };
 cudaError_t launch_sweep_packed(int D, int L, const PackedSweepArgs& a, int gpb, int threads,
                                 cudaStream_t st);
@@ -54,21 +59,28 @@ cudaError_t launch_overlap_packed(const uint64_t* A, const uint64_t* B, int N, i
                                   unsigned long long* hist, cudaStream_t st);
 
 // ---------------- int8 path ----------------
-struct RealSweepArgs {
+struct RealStep {
+    int k, n_sweeps;
+    float beta;
+    uint32_t key0, key1;
+};
+struct RealInst {
     const int8_t* Sin;       // rows of NP bytes (+1/-1)
     int8_t* Sout;
     const int32_t* parent;   // gather rows parent[r] (or null)
     const float* J;          // [D*N] (flushed)
-    const float* h;          // [N] or null
+    const float* h;          // [N] (zeros without a field)
     const longlong2* Jfix;   // [D*N] J * 2^96 as int128 (lo, hi)
-    const longlong2* hfix;   // [N] or null
+    const longlong2* hfix;   // [N]
     longlong2* E;            // [R] energies * 2^96 out
     unsigned long long* cJ;  // [D*N] grad counts of this step (or null)
     unsigned long long* ch;  // [N]
     int R, NP;
-    int k, n_sweeps;
-    float beta;
-    uint32_t key0, key1, c3;
+    uint32_t c3;             // Philox counter word 3 of the WORD stream
+};
+struct RealSweepArgs {
+    RealStep s;
+    RealInst i;
 };
 cudaError_t launch_sweep_real(int D, int L, const RealSweepArgs& a, int warps, int grid,
                               cudaStream_t st);
@@ -77,6 +89,20 @@ cudaError_t launch_init_i8(int8_t* S, int N, int NP, int R, uint32_t k0, uint32_
                            cudaStream_t st);
 cudaError_t launch_overlap_i8(const int8_t* A, const int8_t* B, int N, int NP, int R,
                               unsigned long long* hist, cudaStream_t st);
+
+// ---------------- batched sweep ----------------
+constexpr int kBatchRealBase = 100;   // class ids >= this are real-coupling tiles
+struct BatchSweepInst {
+    int cls;                 // packed: 2 * lattice index (+1 for the doubled groups per block)
+    int pad;
+    PackedInst pk;
+    RealInst re;
+};
+bool batch_class(int D, int L, int kind, int mult, int G, int R, int* cls, int* tiles, size_t* smem);
+cudaError_t batch_sweep_occupancy(size_t smem, int* blocks_per_sm);
+cudaError_t launch_sweep_batched(const PackedStep& ps, const RealStep& rs, const BatchSweepInst* insts,
+                                 const int2* items, int n_items, int mult, int* counter, int blocks,
+                                 size_t smem, cudaStream_t st);
 
 // ---------------- resampling and observables ----------------
 struct ResampleArgs {
@@ -101,6 +127,8 @@ struct ResampleArgs {
 constexpr int kChunk = 1024;     // fixed summation chunk of the weight prefix
 constexpr int kScanBlock = 4096; // elements per block of the copy-number scan
 cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st);
+// all instances of a batch at once: tab[i] describes instance i (device memory)
+cudaError_t launch_resample_batched(const ResampleArgs* tab, int n_inst, int maxR, cudaStream_t st);
 
 struct ObsPartial {
     long long sumE, sumE2, min_lo, min_hi;
@@ -116,6 +144,7 @@ struct ObsArgs {
     StepAcc* cur;
 };
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st);
+cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, cudaStream_t st);
 cudaError_t launch_grad_backward(const unsigned long long* cJ, const unsigned long long* ch,
                                  const double* gbar, const double* betas, int n_temps, int nJ,
                                  int N, int R, double* dJ, double* dh, cudaStream_t st);

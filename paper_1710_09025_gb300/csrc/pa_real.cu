@@ -15,183 +15,27 @@
 //
 // Energies are exact: E * 2^96 is an integer for FP32 couplings of magnitude
 // >= 2^-73, accumulated in int128, so the sum does not depend on order.
-#include "pa_device.cuh"
-#include "pa_internal.h"
+#include "pa_sweep_tiles.cuh"
 
 namespace pa {
 
+// persistent over the instance's tiles of 32 replicas
 template <int D, int L, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) sweep_real_kernel(RealSweepArgs a)
 {
-    using LT = Lat<D, L>;
-    constexpr int N = LT::N, NH = LT::NH;
-    constexpr int NB = (NH + 3) / 4;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    int8_t* T = reinterpret_cast<int8_t*>(smraw);                                   // N*32
-    float* Js = reinterpret_cast<float*>(smraw + N * 32);                            // D*N
-    float* hs = Js + D * N;                                                          // N
-    __int128* Ep = reinterpret_cast<__int128*>(hs + N + ((4 - (((D + 1) * N) & 3)) & 3)); // WARPS*32
-    int* gJ = reinterpret_cast<int*>(Ep + WARPS * 32);                               // D*N
-    int* gh = gJ + D * N;                                                            // N
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool grad = a.cJ != nullptr;
-    for (int t = tid; t < D * N; t += WARPS * 32) Js[t] = a.J[t];
-    for (int t = tid; t < N; t += WARPS * 32) hs[t] = a.h[t];
-    if (grad) {
-        for (int t = tid; t < D * N; t += WARPS * 32) gJ[t] = 0;
-        for (int t = tid; t < N; t += WARPS * 32) gh[t] = 0;
-    }
-    const int ntiles = (a.R + 31) / 32;
-    const int nchunk = a.NP / 16;
-
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int r0 = tile * 32;
-        const int r = r0 + lane;
-        const bool valid = r < a.R;
-        __syncthreads();  // previous tile's epilogue finished with T
-        // ---- prologue: rows (gathered through parent) -> T[parity][q][lane]
-        const int src = valid ? (a.parent ? a.parent[r] : r) : 0;
-        for (int c = warp; c < nchunk; c += WARPS) {
-            uint4 v = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
-            if (valid) v = *reinterpret_cast<const uint4*>(a.Sin + (size_t)src * a.NP + 16 * c);
-            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int i = 16 * c + t;
-                if (i < N) {
-                    const int x = i % L, y = (i / L) % L, z = (D == 3) ? i / (L * L) : 0;
-                    const int p = (x + y + z) & 1;
-                    T[(p * NH + (i >> 1)) * 32 + lane] = (int8_t)(wv[t >> 2] >> (8 * (t & 3)));
-                }
-            }
-        }
-        __syncthreads();
-        // ---- N_S sweeps
-        for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            for (int p = 0; p < 2; ++p) {
-                const uint32_t hsw = 2u * (uint32_t)(a.k * a.n_sweeps + sw) + (uint32_t)p;
-                const int8_t* oth = T + (p ^ 1) * NH * 32;
-                int8_t* cur = T + p * NH * 32;
-                for (int blk = warp; blk < NB; blk += WARPS) {
-                    const u32x4 o = philox((uint32_t)blk, hsw, (uint32_t)r, a.c3, a.key0, a.key1);
-                    const uint32_t rs[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int q = 4 * blk + t;
-                        if (NH % 4 != 0 && q >= NH) break;
-                        const auto nb = LT::neighbours(p, q);
-                        const int si = cur[q * 32 + lane];
-                        float f = 0.0f;
-#pragma unroll
-                        for (int kk = 0; kk < 2 * D; ++kk) {
-                            const int d = kk >> 1;
-                            const float Jb = Js[d * N + ((kk & 1) ? nb.site : nb.site_m[d])];
-                            const int sn = oth[nb.q[kk] * 32 + lane];
-                            const float tt = __int_as_float(__float_as_int(Jb) ^ (sn & (int)0x80000000));
-                            f = (kk == 0) ? tt : add32(f, tt);
-                        }
-                        f = add32(f, hs[nb.site]);
-                        const float dE = mul32(f, si > 0 ? 2.0f : -2.0f);
-                        const float x = mul32(a.beta, dE);
-                        bool acc = x <= 0.0f;
-                        if (!acc) {
-                            const float e = spec_expf(-x);
-                            const unsigned long long thr = __float2ull_rz(mul32(e, 4294967296.0f));
-                            acc = (unsigned long long)rs[t] < thr;
-                        }
-                        if (acc) cur[q * 32 + lane] = (int8_t)(-si);
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        // ---- epilogue: rows out
-        for (int c = warp; c < nchunk; c += WARPS) {
-            uint32_t wv[4] = {0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u};
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int i = 16 * c + t;
-                if (i < N) {
-                    const int x = i % L, y = (i / L) % L, z = (D == 3) ? i / (L * L) : 0;
-                    const int p = (x + y + z) & 1;
-                    const uint32_t b = (uint8_t)T[(p * NH + (i >> 1)) * 32 + lane];
-                    wv[t >> 2] = (wv[t >> 2] & ~(0xFFu << (8 * (t & 3)))) | (b << (8 * (t & 3)));
-                }
-            }
-            if (valid)
-                *reinterpret_cast<uint4*>(a.Sout + (size_t)r * a.NP + 16 * c) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-        }
-        // ---- energies (exact, int128) and gradient counts
-        __int128 e = 0;
-        for (int i = warp; i < N; i += WARPS) {
-            const int x = i % L, y = (i / L) % L, z = (D == 3) ? i / (L * L) : 0;
-            const int p = (x + y + z) & 1;
-            const int si = T[(p * NH + (i >> 1)) * 32 + lane];
-            int nbs[3];
-            nbs[0] = i - x + (x == L - 1 ? 0 : x + 1);
-            nbs[1] = i + ((y == L - 1) ? -(L - 1) * L : L);
-            if (D == 3) nbs[2] = i + ((z == L - 1) ? -(L - 1) * L * L : L * L);
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const int j = nbs[d];
-                const int sj = T[((p ^ 1) * NH + (j >> 1)) * 32 + lane];
-                const longlong2 jf = __ldg(&a.Jfix[d * N + i]);
-                __int128 v = ((__int128)jf.y << 64) | (unsigned long long)jf.x;
-                const int sig = si * sj;
-                e -= (sig > 0) ? v : -v;
-                if (grad) {
-                    const int tot = __reduce_add_sync(0xffffffffu, valid ? sig : 0);
-                    if (lane == 0) gJ[d * N + i] += tot;
-                }
-            }
-            if (a.hfix) {
-                const longlong2 hf = __ldg(&a.hfix[i]);
-                __int128 v = ((__int128)hf.y << 64) | (unsigned long long)hf.x;
-                e -= (si > 0) ? v : -v;
-            }
-            if (grad) {
-                const int tot = __reduce_add_sync(0xffffffffu, valid ? si : 0);
-                if (lane == 0) gh[i] += tot;
-            }
-        }
-        Ep[warp * 32 + lane] = e;
-        __syncthreads();
-        if (warp == 0) {
-            __int128 tot = 0;
-            for (int w = 0; w < WARPS; ++w) tot += Ep[w * 32 + lane];
-            if (valid) {
-                longlong2 out;
-                out.x = (long long)(unsigned long long)tot;
-                out.y = (long long)(tot >> 64);
-                a.E[r] = out;
-            }
-        }
-    }
-    if (grad) {
-        __syncthreads();
-        for (int t = tid; t < D * N; t += WARPS * 32)
-            if (gJ[t]) atomicAdd(&a.cJ[t], (unsigned long long)(long long)gJ[t]);
-        for (int t = tid; t < N; t += WARPS * 32)
-            if (gh[t]) atomicAdd(&a.ch[t], (unsigned long long)(long long)gh[t]);
-    }
-}
-
-template <int D, int L>
-static size_t real_smem(int warps)
-{
-    constexpr int N = Lat<D, L>::N;
-    size_t off = (size_t)N * 32 + (size_t)(D + 1) * N * 4;
-    off = (off + 15) & ~(size_t)15;
-    off += (size_t)warps * 32 * 16;
-    off += (size_t)(D + 1) * N * 4;
-    return off;
+    extern __shared__ __align__(16) unsigned char smem_real[];
+    const bool grad = a.i.cJ != nullptr;
+    real_stage<D, L, WARPS>(a.i, smem_real, grad);
+    const int ntiles = (a.i.R + 31) / 32;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        sweep_real_tile<D, L, WARPS>(a.s, a.i, tile, smem_real, grad);
+    if (grad) real_flush_grad<D, L, WARPS>(a.i, smem_real);
 }
 
 template <int D, int L, int WARPS>
 static cudaError_t launch_real_one(const RealSweepArgs& a, int grid, cudaStream_t st)
 {
-    size_t smem = real_smem<D, L>(WARPS);
+    const size_t smem = RealShape<D, L, WARPS>::SMEM;
     auto kern = sweep_real_kernel<D, L, WARPS>;
     static bool attr_done = false;
     if (!attr_done) {
@@ -204,7 +48,7 @@ static cudaError_t launch_real_one(const RealSweepArgs& a, int grid, cudaStream_
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, WARPS * 32, smem);
-        int ntiles = (a.R + 31) / 32;
+        int ntiles = (a.i.R + 31) / 32;
         grid = sms * (per > 0 ? per : 1);
         if (grid > ntiles) grid = ntiles;
     }

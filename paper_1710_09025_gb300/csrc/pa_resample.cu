@@ -30,10 +30,10 @@ __device__ __forceinline__ double e_minus_min_to_double(const ResampleArgs& a, i
 }
 
 // weights and chunk-local sequential prefix sums (one block per chunk)
-__global__ void __launch_bounds__(256) rs_weights_kernel(ResampleArgs a)
+__device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int c)
 {
     __shared__ double wsh[kChunk];
-    const int c = blockIdx.x, i0 = c * kChunk;
+    const int i0 = c * kChunk;
     const int n = min(kChunk, a.R - i0);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const double d = e_minus_min_to_double(a, i0 + t);
@@ -53,11 +53,17 @@ __global__ void __launch_bounds__(256) rs_weights_kernel(ResampleArgs a)
     __syncthreads();
     for (int t = threadIdx.x; t < n; t += blockDim.x) a.P[i0 + t] = wsh[t];
 }
+__global__ void __launch_bounds__(256) rs_weights_kernel(ResampleArgs a) { rs_weights_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(256) rs_weights_batched(const ResampleArgs* tab)
+{
+    const ResampleArgs& a = tab[blockIdx.y];
+    if ((int)blockIdx.x * kChunk < a.R) rs_weights_body(a, blockIdx.x);
+}
 
 // chunk offsets (sequential), S, ln Q, running free energy
-__global__ void rs_offsets_kernel(ResampleArgs a, int nchunks)
+__device__ __forceinline__ void rs_offsets_body(const ResampleArgs& a)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int nchunks = (a.R + kChunk - 1) / kChunk;
     double T = 0.0;
     for (int c = 0; c < nchunks; ++c) {
         a.T[c] = T;
@@ -79,18 +85,30 @@ __global__ void rs_offsets_kernel(ResampleArgs a, int nchunks)
     a.cur->betaF = __dsub_rn(a.betaF0, sum);
     a.cur->S = S;
 }
-
-__global__ void rs_finalize_kernel(ResampleArgs a)
+__global__ void rs_offsets_kernel(ResampleArgs a)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) rs_offsets_body(a);
+}
+__global__ void rs_offsets_batched(const ResampleArgs* tab, int n_inst)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.R) return;
-    a.P[i] = __dadd_rn(a.T[i / kChunk], a.P[i]);
+    if (i < n_inst) rs_offsets_body(tab[i]);
 }
 
-__global__ void rs_draws_kernel(ResampleArgs a, int nchunks)
+__device__ __forceinline__ void rs_finalize_body(const ResampleArgs& a, int i)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.R) a.P[i] = __dadd_rn(a.T[i / kChunk], a.P[i]);
+}
+__global__ void rs_finalize_kernel(ResampleArgs a) { rs_finalize_body(a, blockIdx.x * blockDim.x + threadIdx.x); }
+__global__ void rs_finalize_batched(const ResampleArgs* tab)
+{
+    rs_finalize_body(tab[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__device__ __forceinline__ void rs_draws_body(const ResampleArgs& a, int q)
+{
     if (q >= a.R) return;
+    const int nchunks = (a.R + kChunk - 1) / kChunk;
     const u32x4 o = philox((uint32_t)q, (uint32_t)a.k, 0u, a.c3, a.key0, a.key1);
     const double S = a.T[nchunks];
     const double x = __dmul_rn(uniform53(o.x, o.y), S);
@@ -110,11 +128,16 @@ __global__ void rs_draws_kernel(ResampleArgs a, int nchunks)
     }
     atomicAdd(&a.counts[lo], 1);
 }
+__global__ void rs_draws_kernel(ResampleArgs a) { rs_draws_body(a, blockIdx.x * blockDim.x + threadIdx.x); }
+__global__ void rs_draws_batched(const ResampleArgs* tab)
+{
+    rs_draws_body(tab[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
 
-__global__ void __launch_bounds__(1024) rs_blocksum_kernel(const int32_t* counts, int R, int32_t* blocksum)
+__device__ __forceinline__ void rs_blocksum_body(const int32_t* counts, int R, int32_t* blocksum, int b)
 {
     __shared__ int ws[32];
-    const int b = blockIdx.x, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     int s = 0;
     for (int t = 0; t < kScanBlock / 1024; ++t) {
         const int i = b * kScanBlock + t * 1024 + tid;
@@ -128,10 +151,18 @@ __global__ void __launch_bounds__(1024) rs_blocksum_kernel(const int32_t* counts
         if (tid == 0) blocksum[b] = v;
     }
 }
-
-__global__ void rs_scan_blocks_kernel(int32_t* blocksum, int nb)
+__global__ void __launch_bounds__(1024) rs_blocksum_kernel(const int32_t* counts, int R, int32_t* blocksum)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    rs_blocksum_body(counts, R, blocksum, blockIdx.x);
+}
+__global__ void __launch_bounds__(1024) rs_blocksum_batched(const ResampleArgs* tab)
+{
+    const ResampleArgs& a = tab[blockIdx.y];
+    if ((int)blockIdx.x * kScanBlock < a.R) rs_blocksum_body(a.counts, a.R, a.blocksum, blockIdx.x);
+}
+
+__device__ __forceinline__ void rs_scan_blocks_body(int32_t* blocksum, int nb)
+{
     int acc = 0;
     for (int b = 0; b < nb; ++b) {
         const int v = blocksum[b];
@@ -139,12 +170,21 @@ __global__ void rs_scan_blocks_kernel(int32_t* blocksum, int nb)
         acc += v;
     }
 }
+__global__ void rs_scan_blocks_kernel(int32_t* blocksum, int nb)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) rs_scan_blocks_body(blocksum, nb);
+}
+__global__ void rs_scan_blocks_batched(const ResampleArgs* tab, int n_inst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_inst) rs_scan_blocks_body(tab[i].blocksum, (tab[i].R + kScanBlock - 1) / kScanBlock);
+}
 
 // exclusive scan inside the block + block offset; write parents and families
-__global__ void __launch_bounds__(1024) rs_fill_kernel(ResampleArgs a)
+__device__ __forceinline__ void rs_fill_body(const ResampleArgs& a, int b)
 {
     __shared__ int ws[32];
-    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int PER = kScanBlock / 1024;
     const int i0 = b * kScanBlock + tid * PER;
     int c[PER];
@@ -188,18 +228,39 @@ __global__ void __launch_bounds__(1024) rs_fill_kernel(ResampleArgs a)
         }
     }
 }
+__global__ void __launch_bounds__(1024) rs_fill_kernel(ResampleArgs a) { rs_fill_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(1024) rs_fill_batched(const ResampleArgs* tab)
+{
+    const ResampleArgs& a = tab[blockIdx.y];
+    if ((int)blockIdx.x * kScanBlock < a.R) rs_fill_body(a, blockIdx.x);
+}
 
 cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
 {
     const int nchunks = (a.R + kChunk - 1) / kChunk;
     const int nb = (a.R + kScanBlock - 1) / kScanBlock;
     rs_weights_kernel<<<nchunks, 256, 0, st>>>(a);
-    rs_offsets_kernel<<<1, 32, 0, st>>>(a, nchunks);
+    rs_offsets_kernel<<<1, 32, 0, st>>>(a);
     rs_finalize_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
-    rs_draws_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a, nchunks);
+    rs_draws_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
     rs_blocksum_kernel<<<nb, 1024, 0, st>>>(a.counts, a.R, a.blocksum);
     rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a.blocksum, nb);
     rs_fill_kernel<<<nb, 1024, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample_batched(const ResampleArgs* tab, int n_inst, int maxR, cudaStream_t st)
+{
+    const unsigned nchunks = (maxR + kChunk - 1) / kChunk;
+    const unsigned nb = (maxR + kScanBlock - 1) / kScanBlock;
+    const unsigned ni = (unsigned)n_inst;
+    rs_weights_batched<<<dim3(nchunks, ni), 256, 0, st>>>(tab);
+    rs_offsets_batched<<<(ni + 63) / 64, 64, 0, st>>>(tab, n_inst);
+    rs_finalize_batched<<<dim3((maxR + 255) / 256, ni), 256, 0, st>>>(tab);
+    rs_draws_batched<<<dim3((maxR + 255) / 256, ni), 256, 0, st>>>(tab);
+    rs_blocksum_batched<<<dim3(nb, ni), 1024, 0, st>>>(tab);
+    rs_scan_blocks_batched<<<(ni + 63) / 64, 64, 0, st>>>(tab, n_inst);
+    rs_fill_batched<<<dim3(nb, ni), 1024, 0, st>>>(tab);
     return cudaGetLastError();
 }
 
@@ -207,7 +268,7 @@ cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
 // kObsBlocks blocks each reduce a contiguous slice of the population in a
 // fixed order; one block combines the partials in block order.  The result
 // does not depend on the GPU (the partition depends only on R).
-__global__ void __launch_bounds__(1024) observe_partial_kernel(ObsArgs a)
+__device__ __forceinline__ void observe_partial_body(const ObsArgs& a)
 {
     __shared__ long long s_ll[2][32];
     __shared__ double s_d[3][32];
@@ -276,10 +337,14 @@ __global__ void __launch_bounds__(1024) observe_partial_kernel(ObsArgs a)
         a.part[blockIdx.x] = p;
     }
 }
-
-__global__ void observe_final_kernel(ObsArgs a)
+__global__ void __launch_bounds__(1024) observe_partial_kernel(ObsArgs a) { observe_partial_body(a); }
+__global__ void __launch_bounds__(1024) observe_partial_batched(const ObsArgs* tab)
 {
-    if (threadIdx.x != 0) return;
+    observe_partial_body(tab[blockIdx.y]);
+}
+
+__device__ __forceinline__ void observe_final_body(const ObsArgs& a)
+{
     long long A = 0, B = 0;
     double C = 0.0, Dd = 0.0, F = 0.0;
     __int128 M = (__int128)(((unsigned __int128)1 << 127) - 1);
@@ -296,11 +361,27 @@ __global__ void observe_final_kernel(ObsArgs a)
     a.cur->emin_lo = (long long)(unsigned long long)M;
     a.cur->emin_hi = (long long)(M >> 64);
 }
+__global__ void observe_final_kernel(ObsArgs a)
+{
+    if (threadIdx.x == 0) observe_final_body(a);
+}
+__global__ void observe_final_batched(const ObsArgs* tab, int n_inst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_inst) observe_final_body(tab[i]);
+}
 
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st)
 {
     observe_partial_kernel<<<kObsBlocks, 1024, 0, st>>>(a);
     observe_final_kernel<<<1, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, cudaStream_t st)
+{
+    observe_partial_batched<<<dim3(kObsBlocks, (unsigned)n_inst), 1024, 0, st>>>(tab);
+    observe_final_batched<<<(n_inst + 63) / 64, 64, 0, st>>>(tab, n_inst);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,510 @@
+// pa_sweep_tiles.cuh -- the Metropolis sweep of one tile of replicas, shared by
+// the single-instance kernels and the batched persistent kernel.
+//
+// Sec. II.B: N_S Metropolis sweeps per temperature; Sec. III.A: checkerboard
+// spin selection (all parity-0 sites, then all parity-1 sites).
+//
+// +-J tile (multi-spin coding): 64 replicas of one instance share a uint64 word
+// per site (bit j = replica 64g+j, bit set = spin -1).  A tile is GPB replica
+// groups staged in shared memory split by parity ([group][parity(i)][i>>1]);
+// all N_S sweeps run there and the tile is written back once per temperature.
+// Flipping S_i changes the energy by dE = 4D - 4n, n = unsatisfied bonds of i
+// (J S_i S_j = -1).  Lanes with dE <= 0 flip; for dE = 4c > 0 a lane flips iff
+// its 32-bit uniform r < thr_c = floor(exp(-beta dE) 2^32).  The uniforms are
+// stored as 32 bit planes (plane b holds bit 31-b of the 64 lanes' r), so
+// r < thr is decided MSB first at the first plane where a lane's bit differs
+// from thr's; planes are generated two at a time only while undecided lanes
+// remain (same decisions as generating all 32).  Energies: per-lane counts of
+// unsatisfied bonds in bit-sliced counters, reduced across the threads of a
+// group with warp shuffles; E = 2 n_unsat - D N.
+//
+// Real-coupling tile: 32 replicas staged transposed to [parity][q][replica]
+// bytes so that a warp (one lane per replica) updates one site of 32
+// replicas; couplings are warp-uniform broadcast loads.  Local field
+// f = ((((t_-x + t_+x) + t_-y) + t_+y) + ...) + h_i in FP32 with t = J S_nb,
+// dE = 2 S_i f (exact), x = f32(beta) dE; accept iff x <= 0 or
+// r < floor(spec_expf(-x) 2^32).  Energies are exact int128 sums of J * 2^96.
+#pragma once
+#include "pa_device.cuh"
+#include "pa_internal.h"
+
+namespace pa {
+
+__device__ __forceinline__ uint64_t maj3(uint64_t a, uint64_t b, uint64_t c)
+{
+    return (a & b) | (c & (a ^ b));
+}
+
+template <int D, int L>
+__device__ __forceinline__ int site_parity(int i)
+{
+    int x = i % L, y = (i / L) % L, z = (D == 3) ? i / (L * L) : 0;
+    return (x + y + z) & 1;
+}
+
+// One plane of the comparison r < thr for the undecided lanes U.  T (the
+// threshold's bit for each lane's class) is selected by the count bits:
+// n = 0 -> v00, n = 1 -> v01, n = 2 -> v10 (0 / ~0 masks of this plane).
+// A lane whose plane bit differs from T is decided: accepted if T = 1.
+__device__ __forceinline__ void plane_step(uint64_t pl, uint32_t v00, uint32_t v01, uint32_t v10,
+                                           uint64_t b0, uint64_t b1, uint64_t& U, uint64_t& acc)
+{
+    const uint64_t V00 = (uint64_t)(int64_t)(int32_t)v00;
+    const uint64_t V01 = (uint64_t)(int64_t)(int32_t)v01;
+    const uint64_t V10 = (uint64_t)(int64_t)(int32_t)v10;
+    const uint64_t inner = (b0 & V01) | (~b0 & V00);
+    const uint64_t T = (b1 & V10) | (~b1 & inner);
+    acc |= U & T & ~pl;
+    U &= ~(T ^ pl);
+}
+
+// bits needed to count up to v
+__host__ __device__ constexpr int bits_for(int v) { return v <= 0 ? 1 : 1 + bits_for(v >> 1); }
+
+template <int D, int L, int GPB, int THREADS>
+struct PackedShape {
+    static constexpr int N = Lat<D, L>::N, NH = Lat<D, L>::NH;
+    static constexpr int TPG = THREADS / GPB;         // threads per group in the energy phase
+    static constexpr int SEGW = TPG < 32 ? TPG : 32;  // shuffle segment width
+    static constexpr int NSEG = TPG / SEGW;           // segments (warps) per group
+    static constexpr int B = bits_for(D * N);         // counter width
+    static constexpr size_t TILE = (size_t)GPB * 2 * NH * 8;
+    static constexpr size_t SJ = ((size_t)N + 15) / 16 * 16;
+    static constexpr size_t CNT = (size_t)GPB * NSEG * B * 8;
+    static constexpr size_t SMEM = TILE + SJ + CNT;
+    static_assert(THREADS % GPB == 0 && (TPG & (TPG - 1)) == 0, "threads per group");
+};
+
+struct Shape {
+    int gpb, threads;
+};
+
+// default groups per block and threads of the packed sweep for a lattice
+template <int D, int L> __host__ __device__ constexpr Shape default_shape()
+{
+    constexpr int N = (D == 3) ? L * L * L : L * L;
+    return N <= 16 ? Shape{32, 256}
+         : N <= 64 ? Shape{8, 256}
+         : N <= 256 ? Shape{8, 256}
+         : N <= 512 ? Shape{4, 256}
+         : N <= 1024 ? Shape{2, 256}
+         : Shape{1, 256};
+}
+
+// groups [g0, g0 + GPB) of one instance; smem holds PackedShape::SMEM bytes
+template <int D, int L, int GPB, int THREADS, bool I8>
+__device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const PackedInst& in, int g0,
+                                                  unsigned char* smem)
+{
+    using LT = Lat<D, L>;
+    using SH = PackedShape<D, L, GPB, THREADS>;
+    constexpr int N = SH::N, NH = SH::NH, TPG = SH::TPG, SEGW = SH::SEGW, NSEG = SH::NSEG, B = SH::B;
+    constexpr int NWARP = THREADS / 32;
+    uint64_t* sm = reinterpret_cast<uint64_t*>(smem);
+    uint8_t* sj = smem + SH::TILE;
+    uint64_t* cnt = reinterpret_cast<uint64_t*>(smem + SH::TILE + SH::SJ);
+
+    const int G = in.G, R = in.R;
+    const uint32_t c3 = in.c3;
+    const int32_t* __restrict__ parent = in.parent;
+    const int ng = min(GPB, G - g0);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+
+    for (int t = tid; t < N; t += THREADS) sj[t] = in.jneg[t];
+
+    if (!I8 && !parent) {
+        for (int t = tid; t < ng * N; t += THREADS) {
+            int gl = t / N, i = t - gl * N;
+            uint64_t w = in.Sin[(size_t)(g0 + gl) * N + i];
+            sm[(gl * 2 + site_parity<D, L>(i)) * NH + (i >> 1)] = w;
+        }
+    } else if (!I8) {
+        // fused resampling gather: lane j of group g takes the bit of replica
+        // parent[64g+j]; parents are non-decreasing, so the 64 sources of a word
+        // sit in one to a few neighbouring groups.  Each thread owns destination
+        // lanes `lane` and `lane+32`; two ballots assemble a word; the word of
+        // site base+t is kept by lane t and stored once per 32 sites.
+        constexpr int NCH = (N + 31) / 32;
+        for (int tup = warp; tup < ng * NCH; tup += NWARP) {
+            const int gl = tup / NCH, base = (tup - gl * NCH) * 32;
+            const int r0 = 64 * (g0 + gl) + lane, r1 = r0 + 32;
+            const int s0 = r0 < R ? parent[r0] : r0;
+            const int s1 = r1 < R ? parent[r1] : r1;
+            const uint64_t* p0 = in.Sin + (size_t)(s0 >> 6) * N + base;
+            const uint64_t* p1 = in.Sin + (size_t)(s1 >> 6) * N + base;
+            const int sb0 = s0 & 63, sb1 = s1 & 63;
+            const int cnt32 = min(32, N - base);
+            uint64_t mine = 0;
+#pragma unroll 4
+            for (int t = 0; t < cnt32; ++t) {
+                const uint64_t w0 = __ldg(p0 + t), w1 = __ldg(p1 + t);
+                const uint32_t lo = __ballot_sync(0xffffffffu, (uint32_t)(w0 >> sb0) & 1u);
+                const uint32_t hi = __ballot_sync(0xffffffffu, (uint32_t)(w1 >> sb1) & 1u);
+                if (lane == t) mine = (uint64_t)lo | ((uint64_t)hi << 32);
+            }
+            const int i = base + lane;
+            if (lane < cnt32) sm[(gl * 2 + site_parity<D, L>(i)) * NH + (i >> 1)] = mine;
+        }
+    } else {
+        // int8 rows -> bit words: one ballot per site and 32-lane half
+        const int nchunk = in.NP / 16;
+        for (int tup = warp; tup < ng * 2 * nchunk; tup += NWARP) {
+            int gl = tup / (2 * nchunk), rem = tup - gl * 2 * nchunk;
+            int h = rem / nchunk, c = rem - h * nchunk;
+            int r = 64 * (g0 + gl) + 32 * h + lane;
+            uint4 v = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+            if (r < R) {
+                int src = parent ? parent[r] : r;
+                v = *reinterpret_cast<const uint4*>(in.S8_in + (size_t)src * in.NP + 16 * c);
+            }
+            uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                int byte = (int)(int8_t)(wv[t >> 2] >> (8 * (t & 3)));
+                uint32_t bal = __ballot_sync(0xffffffffu, byte < 0);
+                int i = 16 * c + t;
+                if (lane == t && i < N)
+                    reinterpret_cast<uint32_t*>(&sm[(gl * 2 + site_parity<D, L>(i)) * NH + (i >> 1)])[h] = bal;
+            }
+        }
+    }
+    __syncthreads();
+
+    const uint64_t und1 = (s.und & 2u) ? ~0ull : 0ull, und2 = (s.und & 4u) ? ~0ull : 0ull,
+                   und3 = (s.und & 8u) ? ~0ull : 0ull;
+    const uint64_t alw1 = (s.always & 2u) ? ~0ull : 0ull, alw2 = (s.always & 4u) ? ~0ull : 0ull,
+                   alw3 = (s.always & 8u) ? ~0ull : 0ull;
+
+    for (int sw = 0; sw < s.n_sweeps; ++sw) {
+        for (int p = 0; p < 2; ++p) {
+            const uint32_t hs = 2u * (uint32_t)(s.k * s.n_sweeps + sw) + (uint32_t)p;
+            for (int t = tid; t < ng * NH; t += THREADS) {
+                const int gl = t / NH, q = t - gl * NH;
+                uint64_t* cur = sm + (gl * 2 + p) * NH;
+                const uint64_t* oth = sm + (gl * 2 + (p ^ 1)) * NH;
+                const auto nb = LT::neighbours(p, q);
+                const uint64_t sw0 = cur[q];
+                const uint32_t jm = sj[nb.site];
+                uint64_t u[2 * D];
+#pragma unroll
+                for (int kk = 0; kk < 2 * D; ++kk)
+                    u[kk] = sw0 ^ oth[nb.q[kk]] ^ (((jm >> kk) & 1u) ? ~0ull : 0ull);
+                uint64_t m1, m2, m3, b0, b1;
+                if (D == 3) {
+                    uint64_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
+                    uint64_t s2 = u[3] ^ u[4] ^ u[5], c2 = maj3(u[3], u[4], u[5]);
+                    b0 = s1 ^ s2;
+                    uint64_t k0 = s1 & s2;
+                    b1 = c1 ^ c2 ^ k0;
+                    uint64_t b2 = maj3(c1, c2, k0);
+                    m3 = ~b2 & ~b1 & ~b0;  // n = 0: dE = 12
+                    m2 = ~b2 & ~b1 & b0;   // n = 1: dE = 8
+                    m1 = ~b2 & b1 & ~b0;   // n = 2: dE = 4
+                } else {
+                    uint64_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
+                    b0 = s1 ^ u[3];
+                    uint64_t k0 = s1 & u[3];
+                    b1 = c1 ^ k0;
+                    uint64_t b2 = c1 & k0;
+                    m3 = 0;
+                    m2 = ~b2 & ~b1 & ~b0;  // n = 0: dE = 8
+                    m1 = ~b2 & ~b1 & b0;   // n = 1: dE = 4
+                }
+                uint64_t acc = ~(m1 | m2 | m3) | (m1 & alw1) | (m2 & alw2) | (m3 & alw3);
+                uint64_t U = (m1 & und1) | (m2 & und2) | (m3 & und3);
+                const uint32_t g = (uint32_t)(g0 + gl);
+                // MSB-first comparison r < thr over the planes still needed
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    if (!U) break;
+                    const u32x4 o = philox_rk((uint32_t)q, hs, 16u * g + (uint32_t)m, c3, s.rk);
+                    plane_step((uint64_t)o.x | ((uint64_t)o.y << 32), s.v00[2 * m], s.v01[2 * m],
+                               s.v10[2 * m], b0, b1, U, acc);
+                    plane_step((uint64_t)o.z | ((uint64_t)o.w << 32), s.v00[2 * m + 1], s.v01[2 * m + 1],
+                               s.v10[2 * m + 1], b0, b1, U, acc);
+                }
+                cur[q] = sw0 ^ acc;
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- write back ----
+    if (!I8) {
+        for (int t = tid; t < ng * N; t += THREADS) {
+            int gl = t / N, i = t - gl * N;
+            in.S[(size_t)(g0 + gl) * N + i] = sm[(gl * 2 + site_parity<D, L>(i)) * NH + (i >> 1)];
+        }
+    } else {
+        const int nchunk = in.NP / 16;
+        for (int tup = warp; tup < ng * 2 * nchunk; tup += NWARP) {
+            int gl = tup / (2 * nchunk), rem = tup - gl * 2 * nchunk;
+            int h = rem / nchunk, c = rem - h * nchunk;
+            int r = 64 * (g0 + gl) + 32 * h + lane;
+            uint32_t wv[4] = {0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u};
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                int i = 16 * c + t;
+                if (i < N) {
+                    uint32_t half = reinterpret_cast<const uint32_t*>(
+                        &sm[(gl * 2 + site_parity<D, L>(i)) * NH + (i >> 1)])[h];
+                    uint32_t byte = ((half >> lane) & 1u) ? 0xFFu : 0x01u;
+                    wv[t >> 2] = (wv[t >> 2] & ~(0xFFu << (8 * (t & 3)))) | (byte << (8 * (t & 3)));
+                }
+            }
+            if (r < R)
+                *reinterpret_cast<uint4*>(in.S8_out + (size_t)r * in.NP + 16 * c) =
+                    make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+    }
+
+    // ---- energies: vertical counters of unsatisfied bonds ----
+    {
+        const int gl = tid / TPG, lt = tid - gl * TPG;
+        uint64_t C[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) C[b] = 0;
+        if (gl < ng) {
+            const uint64_t* base = sm + gl * 2 * NH;
+            for (int i = lt; i < N; i += TPG) {
+                const int x = i % L, y = (i / L) % L, z = (D == 3) ? i / (L * L) : 0;
+                const int p = (x + y + z) & 1;
+                const uint64_t si = base[p * NH + (i >> 1)];
+                const uint32_t jm = sj[i];
+                int nbs[3];
+                nbs[0] = i - x + (x == L - 1 ? 0 : x + 1);
+                nbs[1] = i + ((y == L - 1) ? -(L - 1) * L : L);
+                if (D == 3) nbs[2] = i + ((z == L - 1) ? -(L - 1) * L * L : L * L);
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const int j = nbs[d];
+                    const uint64_t sjw = base[(p ^ 1) * NH + (j >> 1)];
+                    uint64_t carry = si ^ sjw ^ (((jm >> (2 * d + 1)) & 1u) ? ~0ull : 0ull);
+#pragma unroll
+                    for (int b = 0; b < B; ++b) {
+                        uint64_t tt = C[b] & carry;
+                        C[b] ^= carry;
+                        carry = tt;
+                    }
+                }
+            }
+        }
+        // segmented shuffle reduction (bit-sliced addition)
+#pragma unroll
+        for (int off = SEGW / 2; off > 0; off >>= 1) {
+            uint64_t carry = 0;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                uint64_t o = __shfl_xor_sync(0xffffffffu, C[b], off);
+                uint64_t sum = C[b] ^ o ^ carry;
+                carry = maj3(C[b], o, carry);
+                C[b] = sum;
+            }
+        }
+        if (gl < ng && (lt % SEGW) == 0) {
+            const int seg = lt / SEGW;
+#pragma unroll
+            for (int b = 0; b < B; ++b) cnt[(gl * NSEG + seg) * B + b] = C[b];
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < ng * 64; t += THREADS) {
+        const int gl = t >> 6, j = t & 63;
+        int n = 0;
+        for (int seg = 0; seg < NSEG; ++seg)
+#pragma unroll
+            for (int b = 0; b < B; ++b) n += (int)((cnt[(gl * NSEG + seg) * B + b] >> j) & 1ull) << b;
+        const int r = 64 * (g0 + gl) + j;
+        if (r < R) in.E[r] = 2 * n - D * N;
+    }
+    __syncthreads();  // the tile's shared memory is reused by the next tile
+}
+
+// ---------------- real couplings, int8 spins ----------------
+
+template <int D, int L, int WARPS>
+struct RealShape {
+    static constexpr int N = Lat<D, L>::N, NH = Lat<D, L>::NH;
+    static constexpr size_t T8 = (size_t)N * 32;
+    static constexpr size_t JH = (((size_t)(D + 1) * N * 4) + 15) / 16 * 16;
+    static constexpr size_t EP = (size_t)WARPS * 32 * 16;
+    static constexpr size_t GR = (size_t)(D + 1) * N * 4;
+    static constexpr size_t SMEM = T8 + JH + EP + GR;
+};
+
+// couplings and field into shared memory (once per instance)
+template <int D, int L, int WARPS>
+__device__ __forceinline__ void real_stage(const RealInst& in, unsigned char* smem, bool zero_grad)
+{
+    using SH = RealShape<D, L, WARPS>;
+    constexpr int N = SH::N;
+    float* Js = reinterpret_cast<float*>(smem + SH::T8);
+    float* hs = Js + D * N;
+    int* gJ = reinterpret_cast<int*>(smem + SH::T8 + SH::JH + SH::EP);
+    for (int t = threadIdx.x; t < D * N; t += WARPS * 32) Js[t] = in.J[t];
+    for (int t = threadIdx.x; t < N; t += WARPS * 32) hs[t] = in.h[t];
+    if (zero_grad)
+        for (int t = threadIdx.x; t < (D + 1) * N; t += WARPS * 32) gJ[t] = 0;
+    __syncthreads();
+}
+
+// add this block's gradient counts to the step's global counters
+template <int D, int L, int WARPS>
+__device__ __forceinline__ void real_flush_grad(const RealInst& in, unsigned char* smem)
+{
+    using SH = RealShape<D, L, WARPS>;
+    constexpr int N = SH::N;
+    const int* gJ = reinterpret_cast<const int*>(smem + SH::T8 + SH::JH + SH::EP);
+    const int* gh = gJ + D * N;
+    __syncthreads();
+    for (int t = threadIdx.x; t < D * N; t += WARPS * 32)
+        if (gJ[t]) atomicAdd(&in.cJ[t], (unsigned long long)(long long)gJ[t]);
+    for (int t = threadIdx.x; t < N; t += WARPS * 32)
+        if (gh[t]) atomicAdd(&in.ch[t], (unsigned long long)(long long)gh[t]);
+}
+
+// replicas [32 tile, 32 tile + 32) of one instance
+template <int D, int L, int WARPS>
+__device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealInst& in, int tile,
+                                                unsigned char* smem, bool grad)
+{
+    using LT = Lat<D, L>;
+    using SH = RealShape<D, L, WARPS>;
+    constexpr int N = SH::N, NH = SH::NH;
+    constexpr int NB = (NH + 3) / 4;
+    int8_t* T = reinterpret_cast<int8_t*>(smem);
+    const float* Js = reinterpret_cast<const float*>(smem + SH::T8);
+    const float* hs = Js + D * N;
+    __int128* Ep = reinterpret_cast<__int128*>(smem + SH::T8 + SH::JH);
+    int* gJ = reinterpret_cast<int*>(smem + SH::T8 + SH::JH + SH::EP);
+    int* gh = gJ + D * N;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int R = in.R, NP = in.NP;
+    const uint32_t c3 = in.c3;
+    const int nchunk = NP / 16;
+    const int r0 = tile * 32;
+    const int r = r0 + lane;
+    const bool valid = r < R;
+    // ---- prologue: rows (gathered through parent) -> T[parity][q][lane]
+    const int src = valid ? (in.parent ? in.parent[r] : r) : 0;
+    for (int c = warp; c < nchunk; c += WARPS) {
+        uint4 v = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+        if (valid) v = *reinterpret_cast<const uint4*>(in.Sin + (size_t)src * NP + 16 * c);
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int i = 16 * c + t;
+            if (i < N) {
+                const int x = i % L, y = (i / L) % L, z = (D == 3) ? i / (L * L) : 0;
+                const int p = (x + y + z) & 1;
+                T[(p * NH + (i >> 1)) * 32 + lane] = (int8_t)(wv[t >> 2] >> (8 * (t & 3)));
+            }
+        }
+    }
+    __syncthreads();
+    // ---- N_S sweeps
+    for (int sw = 0; sw < s.n_sweeps; ++sw) {
+        for (int p = 0; p < 2; ++p) {
+            const uint32_t hsw = 2u * (uint32_t)(s.k * s.n_sweeps + sw) + (uint32_t)p;
+            const int8_t* oth = T + (p ^ 1) * NH * 32;
+            int8_t* cur = T + p * NH * 32;
+            for (int blk = warp; blk < NB; blk += WARPS) {
+                const u32x4 o = philox((uint32_t)blk, hsw, (uint32_t)r, c3, s.key0, s.key1);
+                const uint32_t rs[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int q = 4 * blk + t;
+                    if (NH % 4 != 0 && q >= NH) break;
+                    const auto nb = LT::neighbours(p, q);
+                    const int si = cur[q * 32 + lane];
+                    float f = 0.0f;
+#pragma unroll
+                    for (int kk = 0; kk < 2 * D; ++kk) {
+                        const int d = kk >> 1;
+                        const float Jb = Js[d * N + ((kk & 1) ? nb.site : nb.site_m[d])];
+                        const int sn = oth[nb.q[kk] * 32 + lane];
+                        const float tt = __int_as_float(__float_as_int(Jb) ^ (sn & (int)0x80000000));
+                        f = (kk == 0) ? tt : add32(f, tt);
+                    }
+                    f = add32(f, hs[nb.site]);
+                    const float dE = mul32(f, si > 0 ? 2.0f : -2.0f);
+                    const float x = mul32(s.beta, dE);
+                    bool acc = x <= 0.0f;
+                    if (!acc) {
+                        const float e = spec_expf(-x);
+                        const unsigned long long thr = __float2ull_rz(mul32(e, 4294967296.0f));
+                        acc = (unsigned long long)rs[t] < thr;
+                    }
+                    if (acc) cur[q * 32 + lane] = (int8_t)(-si);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ---- epilogue: rows out
+    for (int c = warp; c < nchunk; c += WARPS) {
+        uint32_t wv[4] = {0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u};
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int i = 16 * c + t;
+            if (i < N) {
+                const int x = i % L, y = (i / L) % L, z = (D == 3) ? i / (L * L) : 0;
+                const int p = (x + y + z) & 1;
+                const uint32_t b = (uint8_t)T[(p * NH + (i >> 1)) * 32 + lane];
+                wv[t >> 2] = (wv[t >> 2] & ~(0xFFu << (8 * (t & 3)))) | (b << (8 * (t & 3)));
+            }
+        }
+        if (valid)
+            *reinterpret_cast<uint4*>(in.Sout + (size_t)r * NP + 16 * c) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
+    // ---- energies (exact, int128) and gradient counts
+    __int128 e = 0;
+    for (int i = warp; i < N; i += WARPS) {
+        const int x = i % L, y = (i / L) % L, z = (D == 3) ? i / (L * L) : 0;
+        const int p = (x + y + z) & 1;
+        const int si = T[(p * NH + (i >> 1)) * 32 + lane];
+        int nbs[3];
+        nbs[0] = i - x + (x == L - 1 ? 0 : x + 1);
+        nbs[1] = i + ((y == L - 1) ? -(L - 1) * L : L);
+        if (D == 3) nbs[2] = i + ((z == L - 1) ? -(L - 1) * L * L : L * L);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int j = nbs[d];
+            const int sj = T[((p ^ 1) * NH + (j >> 1)) * 32 + lane];
+            const longlong2 jf = __ldg(&in.Jfix[d * N + i]);
+            __int128 v = ((__int128)jf.y << 64) | (unsigned long long)jf.x;
+            const int sig = si * sj;
+            e -= (sig > 0) ? v : -v;
+            if (grad) {
+                const int tot = __reduce_add_sync(0xffffffffu, valid ? sig : 0);
+                if (lane == 0) gJ[d * N + i] += tot;
+            }
+        }
+        {
+            const longlong2 hf = __ldg(&in.hfix[i]);
+            __int128 v = ((__int128)hf.y << 64) | (unsigned long long)hf.x;
+            e -= (si > 0) ? v : -v;
+        }
+        if (grad) {
+            const int tot = __reduce_add_sync(0xffffffffu, valid ? si : 0);
+            if (lane == 0) gh[i] += tot;
+        }
+    }
+    Ep[warp * 32 + lane] = e;
+    __syncthreads();
+    if (warp == 0) {
+        __int128 tot = 0;
+        for (int w = 0; w < WARPS; ++w) tot += Ep[w * 32 + lane];
+        if (valid) {
+            longlong2 out;
+            out.x = (long long)(unsigned long long)tot;
+            out.y = (long long)(tot >> 64);
+            in.E[r] = out;
+        }
+    }
+    __syncthreads();  // T and Ep are reused by the next tile
+}
+
+}  // namespace pa
