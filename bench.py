@@ -270,6 +270,8 @@ def run_gpu(args, wl_name):
     }
     if not args.no_e2e and ws == 1:
         line["e2e"] = e2e_run(P, args, D, L, kind, J, h, R, betas, ns, seed, layout)
+    if not args.no_batched and ws == 1:
+        line["batched_vs_plain"] = batched_vs_plain(P, args)
     if not args.no_cpu_baseline and ws == 1:
         R_s = 1024
         sb = np.array([0.0, 1.25, 2.5, 3.75, 5.0])
@@ -280,6 +282,60 @@ def run_gpu(args, wl_name):
     if ws > 1:
         torch.distributed.destroy_process_group()
     print(json.dumps(line))
+
+
+def batched_vs_plain(P, args):
+    """Disorder batch: 512 instances, L drawn from {4,6,8,10}, half +-J (packed)
+    and half Gaussian (int8), R = 20000 each, 201 temperatures beta in [0,5],
+    N_S = 10.  The same steps run once as batched launches (one persistent
+    sweep launch per step, graph-captured) and once with per-instance launches
+    (pa_anneal_step on each instance); the sampled instances must be identical."""
+    import torch
+    from paper_1710_09025_gb300 import workloads as Wk
+    n_inst, R, K, W0 = 512, 20000, args.batched_steps, 3
+    insts = Wk.batched_instances(n_inst)
+    descs = [dict(L=d["L"], kind=d["kind"], J=d["J"], h=d["h"], R=R, rng_instance=t)
+             for t, d in enumerate(insts)]
+    betas = Wk.schedule_lb(201, 5.0)
+    seed = Wk.BASE_SEED + 2
+    st = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(st):
+        a = P.pa_batch_create(3, descs, betas, 10, seed)
+        b = P.pa_batch_create(3, descs, betas, 10, seed)
+        try:
+            P.pa_batch_run(a, W0)
+            ctxs = [P.pa_batch_instance(b, i) for i in range(n_inst)]
+            for _ in range(W0):
+                for c in ctxs:
+                    P.pa_anneal_step(c)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            P.pa_batch_run(a, K)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms_b = e0.elapsed_time(e1) / K
+            e0.record(st)
+            for _ in range(K):
+                for c in ctxs:
+                    P.pa_anneal_step(c)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms_p = e0.elapsed_time(e1) / K
+            same = all(np.array_equal(P.pa_get_spins(P.pa_batch_instance(a, i)), P.pa_get_spins(ctxs[i]))
+                       for i in range(0, n_inst, 32))
+            cfg = P.pa_batch_sweep_config(a)
+        finally:
+            P.pa_batch_destroy(a)
+            P.pa_batch_destroy(b)
+    att = sum(d["L"] ** 3 for d in descs) * R * 10
+    out.update({"workload": "512 instances, L in {4,6,8,10}, half +-J half Gaussian, R=20000, N_S=10",
+                "timed_k": [W0, W0 + K - 1],
+                "batched_attempts_per_ns": att / (ms_b * 1e6), "plain_attempts_per_ns": att / (ms_p * 1e6),
+                "batched_ms_per_step": ms_b, "plain_ms_per_step": ms_p, "speedup": ms_p / ms_b,
+                "identical_results": bool(same), "sweep_config": cfg})
+    return out
 
 
 def e2e_run(P, args, D, L, kind, J, h, R, betas, ns, seed, layout):
@@ -314,6 +370,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--R", type=int, default=0, help="population override (profiling captures)")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -35,11 +35,12 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_real_kernel(RealSweepArgs a)
 template <int D, int L, int WARPS>
 static cudaError_t launch_real_one(const RealSweepArgs& a, int grid, cudaStream_t st)
 {
-    const size_t smem = RealShape<D, L, WARPS>::SMEM;
+    const size_t smem = a.i.cJ ? RealShape<D, L, WARPS>::SMEM_GRAD : RealShape<D, L, WARPS>::SMEM;
     auto kern = sweep_real_kernel<D, L, WARPS>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)RealShape<D, L, WARPS>::SMEM_GRAD);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }

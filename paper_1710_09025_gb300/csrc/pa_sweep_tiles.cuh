@@ -322,30 +322,57 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
 }
 
 // ---------------- real couplings, int8 spins ----------------
+//
+// Shared memory: the spin tile T[parity][q][32] (bytes), then per site record
+// (parity, q) the couplings to the 2D neighbours in field order, h_i, and the
+// neighbours' byte offsets in the other parity's tile:
+//   Jrec[(p NH + q)] = {J_-x, J_+x, J_-y, J_+y}, {J_-z, J_+z, h_i, offsets 0|1}
+//   Orec[(p NH + q)] = {offsets 2|3, offsets 4|5}      (16-bit each)
+// then (only with gradient counts) the block's integer bond/site sums.  The
+// energy epilogue's int128 partials reuse the spin tile after a barrier.
 
 template <int D, int L, int WARPS>
 struct RealShape {
     static constexpr int N = Lat<D, L>::N, NH = Lat<D, L>::NH;
-    static constexpr size_t T8 = (size_t)N * 32;
-    static constexpr size_t JH = (((size_t)(D + 1) * N * 4) + 15) / 16 * 16;
-    static constexpr size_t EP = (size_t)WARPS * 32 * 16;
+    // spin tile, also holding the epilogue's int128 partials (one per lane and warp)
+    static constexpr size_t T8 = ((size_t)N * 32 > (size_t)WARPS * 32 * 16) ? (size_t)N * 32
+                                                                              : (size_t)WARPS * 32 * 16;
+    static constexpr size_t JREC = (size_t)N * 32;    // 2 x float4 per site
+    static constexpr size_t OREC = (size_t)N * 8;     // uint2 per site
     static constexpr size_t GR = (size_t)(D + 1) * N * 4;
-    static constexpr size_t SMEM = T8 + JH + EP + GR;
+    static constexpr size_t SMEM = T8 + JREC + OREC;
+    static constexpr size_t SMEM_GRAD = SMEM + GR;
+    static_assert(NH * 32 < 65536, "16-bit neighbour offsets");
 };
 
-// couplings and field into shared memory (once per instance)
+// site records (once per instance); zero the block's gradient sums if asked
 template <int D, int L, int WARPS>
 __device__ __forceinline__ void real_stage(const RealInst& in, unsigned char* smem, bool zero_grad)
 {
+    using LT = Lat<D, L>;
     using SH = RealShape<D, L, WARPS>;
-    constexpr int N = SH::N;
-    float* Js = reinterpret_cast<float*>(smem + SH::T8);
-    float* hs = Js + D * N;
-    int* gJ = reinterpret_cast<int*>(smem + SH::T8 + SH::JH + SH::EP);
-    for (int t = threadIdx.x; t < D * N; t += WARPS * 32) Js[t] = in.J[t];
-    for (int t = threadIdx.x; t < N; t += WARPS * 32) hs[t] = in.h[t];
-    if (zero_grad)
+    constexpr int N = SH::N, NH = SH::NH;
+    float4* Jrec = reinterpret_cast<float4*>(smem + SH::T8);
+    uint2* Orec = reinterpret_cast<uint2*>(smem + SH::T8 + SH::JREC);
+    for (int t = threadIdx.x; t < N; t += WARPS * 32) {
+        const int p = t / NH, q = t - p * NH;
+        const auto nb = LT::neighbours(p, q);
+        float Jn[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        uint32_t off[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int kk = 0; kk < 2 * D; ++kk) {
+            const int d = kk >> 1;
+            Jn[kk] = in.J[d * N + ((kk & 1) ? nb.site : nb.site_m[d])];
+            off[kk] = (uint32_t)nb.q[kk] * 32u;
+        }
+        Jrec[2 * t] = make_float4(Jn[0], Jn[1], Jn[2], Jn[3]);
+        Jrec[2 * t + 1] = make_float4(Jn[4], Jn[5], in.h[nb.site], __uint_as_float(off[0] | (off[1] << 16)));
+        Orec[t] = make_uint2(off[2] | (off[3] << 16), off[4] | (off[5] << 16));
+    }
+    if (zero_grad) {
+        int* gJ = reinterpret_cast<int*>(smem + SH::SMEM);
         for (int t = threadIdx.x; t < (D + 1) * N; t += WARPS * 32) gJ[t] = 0;
+    }
     __syncthreads();
 }
 
@@ -355,7 +382,7 @@ __device__ __forceinline__ void real_flush_grad(const RealInst& in, unsigned cha
 {
     using SH = RealShape<D, L, WARPS>;
     constexpr int N = SH::N;
-    const int* gJ = reinterpret_cast<const int*>(smem + SH::T8 + SH::JH + SH::EP);
+    const int* gJ = reinterpret_cast<const int*>(smem + SH::SMEM);
     const int* gh = gJ + D * N;
     __syncthreads();
     for (int t = threadIdx.x; t < D * N; t += WARPS * 32)
@@ -374,10 +401,10 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
     constexpr int N = SH::N, NH = SH::NH;
     constexpr int NB = (NH + 3) / 4;
     int8_t* T = reinterpret_cast<int8_t*>(smem);
-    const float* Js = reinterpret_cast<const float*>(smem + SH::T8);
-    const float* hs = Js + D * N;
-    __int128* Ep = reinterpret_cast<__int128*>(smem + SH::T8 + SH::JH);
-    int* gJ = reinterpret_cast<int*>(smem + SH::T8 + SH::JH + SH::EP);
+    const float4* Jrec = reinterpret_cast<const float4*>(smem + SH::T8);
+    const uint2* Orec = reinterpret_cast<const uint2*>(smem + SH::T8 + SH::JREC);
+    __int128* Ep = reinterpret_cast<__int128*>(smem);  // reuses the spin tile after the epilogue
+    int* gJ = reinterpret_cast<int*>(smem + SH::SMEM);
     int* gh = gJ + D * N;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -417,25 +444,29 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
                 for (int t = 0; t < 4; ++t) {
                     const int q = 4 * blk + t;
                     if (NH % 4 != 0 && q >= NH) break;
-                    const auto nb = LT::neighbours(p, q);
+                    const int rec = p * NH + q;
+                    const float4 ja = Jrec[2 * rec], jb = Jrec[2 * rec + 1];
+                    const uint2 ob = Orec[rec];
+                    const uint32_t o01 = __float_as_uint(jb.w);
+                    const float Jn[6] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y};
+                    const uint32_t off[6] = {o01 & 0xFFFFu, o01 >> 16, ob.x & 0xFFFFu, ob.x >> 16,
+                                             ob.y & 0xFFFFu, ob.y >> 16};
                     const int si = cur[q * 32 + lane];
                     float f = 0.0f;
 #pragma unroll
                     for (int kk = 0; kk < 2 * D; ++kk) {
-                        const int d = kk >> 1;
-                        const float Jb = Js[d * N + ((kk & 1) ? nb.site : nb.site_m[d])];
-                        const int sn = oth[nb.q[kk] * 32 + lane];
-                        const float tt = __int_as_float(__float_as_int(Jb) ^ (sn & (int)0x80000000));
+                        const int sn = oth[off[kk] + lane];
+                        const float tt = __int_as_float(__float_as_int(Jn[kk]) ^ (sn & (int)0x80000000));
                         f = (kk == 0) ? tt : add32(f, tt);
                     }
-                    f = add32(f, hs[nb.site]);
+                    f = add32(f, jb.z);
                     const float dE = mul32(f, si > 0 ? 2.0f : -2.0f);
                     const float x = mul32(s.beta, dE);
                     bool acc = x <= 0.0f;
                     if (!acc) {
+                        // thr = floor(e 2^32) <= 2^32; e == 1 accepts every r
                         const float e = spec_expf(-x);
-                        const unsigned long long thr = __float2ull_rz(mul32(e, 4294967296.0f));
-                        acc = (unsigned long long)rs[t] < thr;
+                        acc = (e == 1.0f) || (rs[t] < __float2uint_rz(mul32(e, 4294967296.0f)));
                     }
                     if (acc) cur[q * 32 + lane] = (int8_t)(-si);
                 }
@@ -492,6 +523,7 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
             if (lane == 0) gh[i] += tot;
         }
     }
+    __syncthreads();  // every warp is done reading the spin tile
     Ep[warp * 32 + lane] = e;
     __syncthreads();
     if (warp == 0) {
