@@ -431,6 +431,11 @@ static void fill_packed_step(pa::PackedStep* s, int D, double beta, int k, int n
         if (t >= 4294967296ull) s->always |= 1u << cl;
         else if (t > 0) s->und |= 1u << cl;
     }
+    // undecided class sets with a cheaper comparison loop (thresholds fall with
+    // dE, so classes never accepted are the large-dE ones)
+    if (s->always == 0 && s->und == 2u) s->mode = 1;
+    else if (s->always == 0 && s->und == 6u) s->mode = 2;
+    else s->mode = 0;
     for (int r = 0; r < 10; ++r) {
         s->rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
         s->rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;

@@ -304,6 +304,29 @@ struct Lat {
         }
         return nb;
     }
+    // the same for a site whose column (xh, y) is known (3D): only z is decoded
+    static __device__ __forceinline__ Nb neighbours_column(int p, int q, int xh, int y)
+    {
+        static_assert(D == 3, "column walk is three-dimensional");
+        Nb nb;
+        const int z = q / (LH * L);
+        const int b = (p + y + z) & 1;
+        nb.site = 2 * q + b;
+        // x: b = 0 -> (q - 1 or row wrap, q); b = 1 -> (q, q + 1 or row wrap)
+        const int dxm = b ? 0 : (xh == 0 ? LH - 1 : -1);
+        const int dxp = b ? (xh == LH - 1 ? -(LH - 1) : 1) : 0;
+        nb.q[0] = q + dxm;
+        nb.q[1] = q + dxp;
+        nb.q[2] = q + (y == 0 ? (L - 1) * LH : -LH);
+        nb.q[3] = q + (y == L - 1 ? -(L - 1) * LH : LH);
+        nb.q[4] = q + (z == 0 ? (L - 1) * LH * L : -LH * L);
+        nb.q[5] = q + (z == L - 1 ? -(L - 1) * LH * L : LH * L);
+        const int x = 2 * xh + b;
+        nb.site_m[0] = x == 0 ? nb.site + (L - 1) : nb.site - 1;
+        nb.site_m[1] = (y == 0) ? nb.site + (L - 1) * L : nb.site - L;
+        nb.site_m[2] = (z == 0) ? nb.site + (L - 1) * L * L : nb.site - L * L;
+        return nb;
+    }
 };
 
 }  // namespace pa

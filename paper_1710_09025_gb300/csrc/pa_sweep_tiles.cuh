@@ -58,6 +58,29 @@ __device__ __forceinline__ void plane_step(uint64_t pl, uint32_t v00, uint32_t v
     U &= ~(T ^ pl);
 }
 
+// The same step when every undecided lane has the same threshold: its plane
+// bit t is uniform, so the decision needs no per-lane selection.
+__device__ __forceinline__ void plane_step_uniform(uint64_t pl, uint32_t t, uint64_t& U, uint64_t& acc)
+{
+    if (t) {
+        acc |= U & ~pl;
+        U &= pl;
+    } else {
+        U &= ~pl;
+    }
+}
+
+// Two classes: sel picks the class with threshold bit ta (sel = 1) or tb.
+__device__ __forceinline__ void plane_step_two(uint64_t pl, uint32_t ta, uint32_t tb, uint64_t sel,
+                                               uint64_t& U, uint64_t& acc)
+{
+    const uint64_t A = (uint64_t)(int64_t)(int32_t)ta;
+    const uint64_t B = (uint64_t)(int64_t)(int32_t)tb;
+    const uint64_t T = (sel & A) | (~sel & B);
+    acc |= U & T & ~pl;
+    U &= ~(T ^ pl);
+}
+
 // bits needed to count up to v
 __host__ __device__ constexpr int bits_for(int v) { return v <= 0 ? 1 : 1 + bits_for(v >> 1); }
 
@@ -176,20 +199,37 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     const uint64_t alw1 = (s.always & 2u) ? ~0ull : 0ull, alw2 = (s.always & 4u) ? ~0ull : 0ull,
                    alw3 = (s.always & 8u) ? ~0ull : 0ull;
 
+    // this thread's x-y column (used when every item of the thread shares it)
+    const int xh_c = (tid % NH) % LT::LH, y_c = ((tid % NH) / LT::LH) % L;
     for (int sw = 0; sw < s.n_sweeps; ++sw) {
         for (int p = 0; p < 2; ++p) {
             const uint32_t hs = 2u * (uint32_t)(s.k * s.n_sweeps + sw) + (uint32_t)p;
+            // neighbour decoding: when every item of this thread sits on the same
+            // sublattice site (THREADS a multiple of N/2) decode once; when it sits
+            // on the same x-y column (3D, THREADS a multiple of L^2/2) only z moves
+            typename LT::Nb nb_fixed;
+            if constexpr (THREADS % NH == 0) nb_fixed = LT::neighbours(p, tid % NH);
             for (int t = tid; t < ng * NH; t += THREADS) {
                 const int gl = t / NH, q = t - gl * NH;
                 uint64_t* cur = sm + (gl * 2 + p) * NH;
                 const uint64_t* oth = sm + (gl * 2 + (p ^ 1)) * NH;
-                const auto nb = LT::neighbours(p, q);
+                typename LT::Nb nb;
+                if constexpr (THREADS % NH == 0) {
+                    nb = nb_fixed;
+                } else if constexpr (D == 3 && THREADS % (LT::LH * L) == 0) {
+                    nb = LT::neighbours_column(p, q, xh_c, y_c);
+                } else {
+                    nb = LT::neighbours(p, q);
+                }
                 const uint64_t sw0 = cur[q];
                 const uint32_t jm = sj[nb.site];
                 uint64_t u[2 * D];
 #pragma unroll
-                for (int kk = 0; kk < 2 * D; ++kk)
-                    u[kk] = sw0 ^ oth[nb.q[kk]] ^ (((jm >> kk) & 1u) ? ~0ull : 0ull);
+                for (int kk = 0; kk < 2 * D; ++kk) {
+                    // coupling sign of bond kk as a 0 / ~0 mask (bit kk sign-extended)
+                    const uint32_t m32 = (uint32_t)((int32_t)(jm << (31 - kk)) >> 31);
+                    u[kk] = sw0 ^ oth[nb.q[kk]] ^ (((uint64_t)m32 << 32) | m32);
+                }
                 uint64_t m1, m2, m3, b0, b1;
                 if (D == 3) {
                     uint64_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
@@ -212,17 +252,46 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     m1 = ~b2 & ~b1 & b0;   // n = 1: dE = 4
                 }
                 uint64_t acc = ~(m1 | m2 | m3) | (m1 & alw1) | (m2 & alw2) | (m3 & alw3);
-                uint64_t U = (m1 & und1) | (m2 & und2) | (m3 & und3);
                 const uint32_t g = (uint32_t)(g0 + gl);
                 // MSB-first comparison r < thr over the planes still needed
+                if (s.mode == 1) {
+                    // only dE = 4 lanes are undecided: one threshold, its plane bit is uniform
+                    uint64_t U = m1;
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    if (!U) break;
-                    const u32x4 o = philox_rk((uint32_t)q, hs, 16u * g + (uint32_t)m, c3, s.rk);
-                    plane_step((uint64_t)o.x | ((uint64_t)o.y << 32), s.v00[2 * m], s.v01[2 * m],
-                               s.v10[2 * m], b0, b1, U, acc);
-                    plane_step((uint64_t)o.z | ((uint64_t)o.w << 32), s.v00[2 * m + 1], s.v01[2 * m + 1],
-                               s.v10[2 * m + 1], b0, b1, U, acc);
+                    for (int m = 0; m < 16; ++m) {
+                        if (!U) break;
+                        const u32x4 o = philox_rk((uint32_t)q, hs, 16u * g + (uint32_t)m, c3, s.rk);
+                        // the dE = 4 class has n = 2 unsatisfied bonds in 3D (v10), n = 1 in 2D (v01)
+                        plane_step_uniform((uint64_t)o.x | ((uint64_t)o.y << 32),
+                                           (D == 3) ? s.v10[2 * m] : s.v01[2 * m], U, acc);
+                        plane_step_uniform((uint64_t)o.z | ((uint64_t)o.w << 32),
+                                           (D == 3) ? s.v10[2 * m + 1] : s.v01[2 * m + 1], U, acc);
+                    }
+                } else if (s.mode == 2) {
+                    // dE = 4 and dE = 8 lanes: the threshold bit is picked by one count bit
+                    uint64_t U = m1 | m2;
+                    const uint64_t sel = (D == 3) ? b1 : b0;  // 1 selects the dE = 4 class
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        if (!U) break;
+                        const u32x4 o = philox_rk((uint32_t)q, hs, 16u * g + (uint32_t)m, c3, s.rk);
+                        plane_step_two((uint64_t)o.x | ((uint64_t)o.y << 32), (D == 3) ? s.v10[2 * m] : s.v01[2 * m],
+                                       (D == 3) ? s.v01[2 * m] : s.v00[2 * m], sel, U, acc);
+                        plane_step_two((uint64_t)o.z | ((uint64_t)o.w << 32),
+                                       (D == 3) ? s.v10[2 * m + 1] : s.v01[2 * m + 1],
+                                       (D == 3) ? s.v01[2 * m + 1] : s.v00[2 * m + 1], sel, U, acc);
+                    }
+                } else {
+                    uint64_t U = (m1 & und1) | (m2 & und2) | (m3 & und3);
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        if (!U) break;
+                        const u32x4 o = philox_rk((uint32_t)q, hs, 16u * g + (uint32_t)m, c3, s.rk);
+                        plane_step((uint64_t)o.x | ((uint64_t)o.y << 32), s.v00[2 * m], s.v01[2 * m],
+                                   s.v10[2 * m], b0, b1, U, acc);
+                        plane_step((uint64_t)o.z | ((uint64_t)o.w << 32), s.v00[2 * m + 1], s.v01[2 * m + 1],
+                                   s.v10[2 * m + 1], b0, b1, U, acc);
+                    }
                 }
                 cur[q] = sw0 ^ acc;
             }
