@@ -39,7 +39,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spin-flip attempts/ns on 1 GB300 (% HBM roofline); batched vs plain speedup"
 UNIT = "attempts/ns"
-BYTES_PER_ATTEMPT = 0.25  # per-sweep streaming: 1/8 byte read + 1/8 byte written per attempt
+# per-sweep streaming bytes per attempted flip: one spin read and written per
+# sweep (packed: 1 bit each way; int8: 1 byte each way)
+BYTES_PER_ATTEMPT = {"packed": 0.25, "i8": 2.0}
 
 
 def _peaks():
@@ -56,6 +58,24 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    """Max of x over the ranks of the initialised process group (x itself
+    without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(ms_local: float, attempts_per_step: int, steps: int, world: int, device="cpu"):
+    """Whole-job throughput: all ranks' attempts over the slowest rank's time."""
+    ms = max_over_ranks(ms_local, device)
+    return world * steps * attempts_per_step / (ms * 1e6), ms
 
 
 class ClockSampler:
@@ -119,17 +139,21 @@ def _sweep_profile_traffic():
         d = json.load(open(p))
     except Exception:
         return None
-    src = open(os.path.join(ROOT, "paper_1710_09025_gb300", "csrc", "pa_packed.cu"), "rb").read()
-    if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    # the hash of the kernel's sources at capture time (sha256 of the files' sha256 lines)
+    lines = ""
+    for f in d.get("source_files", []):
+        digest = hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest()
+        lines += f"{digest}  {f}\n"
+    if not lines or d.get("source_sha256") != hashlib.sha256(lines.encode()).hexdigest():
         return None
     return d.get("dram_bytes_per_full_launch")
 
 
-def oracle_rate(D, L, J, R_sample, betas, n_sweeps, seed, steps=None):
+def oracle_rate(D, L, J, R_sample, betas, n_sweeps, seed, steps=None, kind=0, h=None):
     """Oracle attempts/ns on a bounded sample (single thread)."""
     from oracle import oracle as O
     O.build()
-    s = O.Sim(D, L, O.PM1, J, None, R_sample, betas, n_sweeps, seed)
+    s = O.Sim(D, L, kind, J, h, R_sample, betas, n_sweeps, seed)
     N = L ** D
     t0 = time.perf_counter()
     n = 0
@@ -144,13 +168,13 @@ def oracle_rate(D, L, J, R_sample, betas, n_sweeps, seed, steps=None):
 def run_reference(args, wl_name):
     from paper_1710_09025_gb300 import workloads as Wk
     w = Wk.WORKLOADS[wl_name]
-    J, _, betas = Wk.workload_inputs(wl_name)
+    J, h, betas = Wk.workload_inputs(wl_name)
     D, L, ns = w["D"], w["L"], w["n_sweeps"]
-    R_s = 128
+    R_s = 128 if w["kind"] == 0 else 32
     betas = _schedule(betas, args.warmup + args.steps)
     from oracle import oracle as O
     O.build()
-    s = O.Sim(D, L, O.PM1, J, None, R_s, betas, ns, w["seed"])
+    s = O.Sim(D, L, w["kind"], J, h, R_s, betas, ns, w["seed"])
     for _ in range(args.warmup):
         s.step()
     t0 = time.perf_counter()
@@ -220,14 +244,9 @@ def run_gpu(args, wl_name):
     if ws > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
     phase_ms, phase_n, launches1 = P.pa_phase_times(ctx)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     attempts_step = N * R * ns
-    value = ws * args.steps * attempts_step / (ms * 1e6)
+    value, ms = aggregate(e0.elapsed_time(e1), attempts_step, args.steps, ws, device="cuda")
     obs_last = P.pa_observables(ctx, args.warmup + args.steps - 1)
     pop.close()
     if rank != 0:
@@ -237,16 +256,18 @@ def run_gpu(args, wl_name):
 
     peak, peak_kind = _peaks()
     sweep_ms = phase_ms["sweep"] / max(phase_n["sweep"], 1)
-    bytes_launch = BYTES_PER_ATTEMPT * attempts_step
+    bytes_launch = BYTES_PER_ATTEMPT[w["layout"]] * attempts_step
     achieved = bytes_launch / (sweep_ms * 1e-3) / 1e9
-    traffic = _sweep_profile_traffic()
+    traffic = _sweep_profile_traffic() if w["layout"] == "packed" else None
     rs_ms = phase_ms["resample"] / max(phase_n["resample"], 1)
     per_step = {k: phase_ms[k] / max(phase_n[k], 1) for k in ("resample", "gather", "sweep", "observe")}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64" if w["layout"] == "packed" else "i8 spins, f32 fields, int128 energies",
+        "data": "synthetic",
         "config": {"workload": wl_name, "D": D, "L": L, "N": N, "R": R, "n_temps": len(betas),
                    "n_sweeps": ns, "layout": w["layout"], "couplings": "+-J" if kind == 0 else "gaussian",
                    "schedule": "linear in beta, 0..%g" % w["beta_max"],
@@ -254,12 +275,13 @@ def run_gpu(args, wl_name):
                    "l2": "state 2 x %.0f MB > 129 MB L2 (no flush needed)" % (8 * N * ((R + 63) // 64) / 1e6),
                    "parallelism": "one independent instance per GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "sweep_packed_kernel",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "sweep_packed_kernel" if w["layout"] == "packed" else "sweep_real_kernel",
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_launch,
-                     "note": "0.25 B per attempted flip (spin bit read + written per sweep); the "
-                             "kernel keeps the state in shared memory for all N_S sweeps and is "
-                             "bound by integer ALU (Philox), see alu_note"},
+                     "note": "per-sweep streaming bytes per attempted flip (spin read + written "
+                             "each sweep); the kernel keeps the state in shared memory for all N_S "
+                             "sweeps and is bound by integer ALU issue, not DRAM"},
         "phases_ms_per_step": per_step,
         "sweep_attempts_per_ns": attempts_step / (sweep_ms * 1e6),
         "resampled_replicas_per_s": R / (rs_ms * 1e-3) if rs_ms > 0 else None,
@@ -273,9 +295,9 @@ def run_gpu(args, wl_name):
     if not args.no_batched and ws == 1:
         line["batched_vs_plain"] = batched_vs_plain(P, args)
     if not args.no_cpu_baseline and ws == 1:
-        R_s = 1024
+        R_s = 1024 if kind == 0 else 64
         sb = np.array([0.0, 1.25, 2.5, 3.75, 5.0])
-        v, n, dt = oracle_rate(D, L, J, R_s, sb, ns, w["seed"])
+        v, n, dt = oracle_rate(D, L, J, R_s, sb, ns, w["seed"], kind=kind, h=h)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{wl_name} lattice and couplings, R'={R_s} replicas, "
                                           f"beta in {list(sb)}, N_S={ns}: {n} steps in {dt:.1f} s"}

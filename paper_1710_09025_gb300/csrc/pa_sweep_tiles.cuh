@@ -509,10 +509,13 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
             for (int blk = warp; blk < NB; blk += WARPS) {
                 const u32x4 o = philox((uint32_t)blk, hsw, (uint32_t)r, c3, s.key0, s.key1);
                 const uint32_t rs[4] = {o.x, o.y, o.z, o.w};
+                // the four sites of one random-number block are independent (same
+                // parity): fields and energy changes first, then decisions, then stores
+                float xs[4];
+                int sis[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const int q = 4 * blk + t;
-                    if (NH % 4 != 0 && q >= NH) break;
+                    const int q = (NH % 4 != 0 && 4 * blk + t >= NH) ? 4 * blk : 4 * blk + t;
                     const int rec = p * NH + q;
                     const float4 ja = Jrec[2 * rec], jb = Jrec[2 * rec + 1];
                     const uint2 ob = Orec[rec];
@@ -530,14 +533,23 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
                     }
                     f = add32(f, jb.z);
                     const float dE = mul32(f, si > 0 ? 2.0f : -2.0f);
-                    const float x = mul32(s.beta, dE);
-                    bool acc = x <= 0.0f;
-                    if (!acc) {
-                        // thr = floor(e 2^32) <= 2^32; e == 1 accepts every r
-                        const float e = spec_expf(-x);
-                        acc = (e == 1.0f) || (rs[t] < __float2uint_rz(mul32(e, 4294967296.0f)));
-                    }
-                    if (acc) cur[q * 32 + lane] = (int8_t)(-si);
+                    xs[t] = mul32(s.beta, dE);
+                    sis[t] = si;
+                }
+                bool accs[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    // x <= 0 accepts; else r < floor(e 2^32) with e = exp(-x), and
+                    // e == 1 (thr = 2^32) accepts every r
+                    const float e = spec_expf(fminf(-xs[t], 0.0f));
+                    accs[t] = (xs[t] <= 0.0f) || (e == 1.0f) ||
+                              (rs[t] < __float2uint_rz(mul32(e, 4294967296.0f)));
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int q = 4 * blk + t;
+                    if (NH % 4 != 0 && q >= NH) break;
+                    if (accs[t]) cur[q * 32 + lane] = (int8_t)(-sis[t]);
                 }
             }
             __syncthreads();

@@ -71,6 +71,9 @@ WORKLOADS = {
                              pm_couplings=True),
     "ea3d_L6_gauss_R5e4": dict(D=3, L=6, kind=REAL, R=50_000, n_temps=101, beta_max=3.0,
                                n_sweeps=10, layout="i8", seed=BASE_SEED + 33),
+    # one Gaussian instance of the disorder batch at its largest size
+    "ea3d_L10_gauss_R2e4": dict(D=3, L=10, kind=REAL, R=20_000, n_temps=201, beta_max=5.0,
+                                n_sweeps=10, layout="i8", seed=BASE_SEED + 10),
 }
 
 
