@@ -63,6 +63,13 @@ typedef struct or_sim or_sim;
 or_sim* or_create(int D, int L, int kind, const float* J, const float* h, int R,
                   const double* betas, int n_temps, int n_sweeps, uint64_t seed,
                   uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad);
+/* dynamic population (Sec. III.D, Eq. 6): populations[k] replicas at temperature
+ * k, 1 <= populations[k] <= R (R is the capacity); NULL keeps R throughout */
+or_sim* or_create_dps(int D, int L, int kind, const float* J, const float* h, int R,
+                      const double* betas, int n_temps, int n_sweeps, uint64_t seed,
+                      uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad,
+                      const int32_t* populations);
+int     or_current_R(const or_sim* s);
 void    or_destroy(or_sim* s);
 /* runs temperature index k = next step; returns k, or -1 after the last one */
 int     or_step(or_sim* s);

@@ -69,6 +69,8 @@ def lib():
                 "or_counter3": (u32, [u32, u32, u32]),
                 "or_lattice": (i32, [i32, i32, vp, vp]),
                 "or_create": (vp, [i32, i32, i32, vp, vp, i32, vp, i32, i32, u64, u32, u32, i32]),
+                "or_create_dps": (vp, [i32, i32, i32, vp, vp, i32, vp, i32, i32, u64, u32, u32, i32, vp]),
+                "or_current_R": (i32, [vp]),
                 "or_destroy": (None, [vp]),
                 "or_step": (i32, [vp]),
                 "or_next_step": (i32, [vp]),
@@ -229,7 +231,7 @@ class Sim:
     """One oracle PAMC run (Sec. II.B), stepped one temperature at a time."""
 
     def __init__(self, D, L, kind, J, h, R, betas, n_sweeps, seed, rng_instance=0, rng_tag=0,
-                 accumulate_grad=False):
+                 accumulate_grad=False, populations=None):
         self.D, self.L, self.kind, self.R = D, L, kind, R
         self.N = L ** D
         self.betas = np.ascontiguousarray(betas, dtype=np.float64)
@@ -237,9 +239,10 @@ class Sim:
         self.J = np.ascontiguousarray(J, dtype=np.float32)
         self.h = None if h is None else np.ascontiguousarray(h, dtype=np.float32)
         self.acc = bool(accumulate_grad)
-        self._h = lib().or_create(D, L, kind, _p(self.J), _p(self.h), R, _p(self.betas),
-                                  self.n_temps, n_sweeps, seed, rng_instance, rng_tag,
-                                  int(accumulate_grad))
+        self.populations = None if populations is None else np.ascontiguousarray(populations, np.int32)
+        self._h = lib().or_create_dps(D, L, kind, _p(self.J), _p(self.h), R, _p(self.betas),
+                                      self.n_temps, n_sweeps, seed, rng_instance, rng_tag,
+                                      int(accumulate_grad), _p(self.populations))
         if not self._h:
             raise ValueError("oracle rejected the configuration")
 
@@ -260,8 +263,13 @@ class Sim:
     def k_next(self):
         return lib().or_next_step(self._h)
 
+    @property
+    def R_now(self):
+        """Current population (changes per step with a dynamic population)."""
+        return lib().or_current_R(self._h)
+
     def spins(self):
-        out = np.empty((self.R, self.N), np.int8)
+        out = np.empty((self.R_now, self.N), np.int8)
         lib().or_get_spins(self._h, _p(out))
         return out
 
@@ -270,7 +278,7 @@ class Sim:
         lib().or_set_spins(self._h, _p(s))
 
     def energies_raw(self):
-        out = np.empty(2 * self.R, np.int64)
+        out = np.empty(2 * self.R_now, np.int64)
         lib().or_get_energies(self._h, _p(out))
         return out
 
@@ -279,12 +287,12 @@ class Sim:
         return int128_pairs(self.energies_raw())
 
     def parents(self):
-        out = np.empty(self.R, np.int32)
+        out = np.empty(self.R_now, np.int32)
         lib().or_get_parents(self._h, _p(out))
         return out
 
     def family(self):
-        out = np.empty(self.R, np.int32)
+        out = np.empty(self.R_now, np.int32)
         lib().or_get_family(self._h, _p(out))
         return out
 

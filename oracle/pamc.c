@@ -46,6 +46,8 @@ typedef __int128 i128;
 
 struct or_sim {
     int D, L, N, kind, R, G, n_temps, n_sweeps, k_next, acc_grad;
+    int Rcap, R_src_last;      /* capacity; source population of the last resampling */
+    int32_t* Rk;               /* population at each temperature (Sec. III.D, Eq. 6) */
     uint64_t seed;
     uint32_t inst, tag;
     float *J, *h;
@@ -259,9 +261,13 @@ static double e_to_double(int kind, i128 v)
     return (kind == OR_PM1) ? (double)v : (double)v * 0x1p-96;
 }
 
-static int resample_core(int kind, int R, const i128* E, double beta_prev, double beta_next, int k,
-                         uint64_t seed, uint32_t inst, uint32_t tag, double* w, double* P,
-                         int32_t* parent, int32_t* counts, double* lnQ, double* u_out)
+/* Resampling R (source replicas) -> Rn (new population): Rn multinomial draws
+ * with probabilities w_i / S, so replica i gets Rn w_i / S copies on average
+ * and the expected new population is Rn (Sec. II.B; Rn = R(beta') of Sec.
+ * III.D, Eq. 6, for a dynamic population).  Q averages over the R sources. */
+static int resample_core2(int kind, int R, int Rn, const i128* E, double beta_prev, double beta_next,
+                          int k, uint64_t seed, uint32_t inst, uint32_t tag, double* w, double* P,
+                          int32_t* parent, int32_t* counts, double* lnQ, double* u_out)
 {
     double db = beta_next - beta_prev;
     i128 emin = E[0];
@@ -287,7 +293,7 @@ static int resample_core(int kind, int R, const i128* E, double beta_prev, doubl
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t c3 = or_counter3(OR_STREAM_RESAMPLE, tag, inst);
     memset(counts, 0, sizeof(int32_t) * (size_t)R);
-    for (int q = 0; q < R; ++q) {
+    for (int q = 0; q < Rn; ++q) {
         uint32_t ctr[4] = {(uint32_t)q, (uint32_t)k, 0u, c3}, out[4];
         or_philox4x32_10(ctr, key, out);
         double u = or_uniform53(out[0], out[1]);
@@ -311,7 +317,15 @@ static int resample_core(int kind, int R, const i128* E, double beta_prev, doubl
     int j = 0;
     for (int i = 0; i < R; ++i)
         for (int t = 0; t < counts[i]; ++t) parent[j++] = i;
-    return j == R ? 0 : -1;
+    return j == Rn ? 0 : -1;
+}
+
+static int resample_core(int kind, int R, const i128* E, double beta_prev, double beta_next, int k,
+                         uint64_t seed, uint32_t inst, uint32_t tag, double* w, double* P,
+                         int32_t* parent, int32_t* counts, double* lnQ, double* u_out)
+{
+    return resample_core2(kind, R, R, E, beta_prev, beta_next, k, seed, inst, tag, w, P, parent,
+                          counts, lnQ, u_out);
 }
 
 int or_resample(int kind, int R, const int64_t* E, double beta_prev, double beta_next, int k,
@@ -344,6 +358,18 @@ or_sim* or_create(int D, int L, int kind, const float* J, const float* h, int R,
                   const double* betas, int n_temps, int n_sweeps, uint64_t seed,
                   uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad)
 {
+    return or_create_dps(D, L, kind, J, h, R, betas, n_temps, n_sweeps, seed, rng_instance, rng_tag,
+                         accumulate_grad, NULL);
+}
+
+or_sim* or_create_dps(int D, int L, int kind, const float* J, const float* h, int R,
+                      const double* betas, int n_temps, int n_sweeps, uint64_t seed,
+                      uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad,
+                      const int32_t* populations)
+{
+    if (populations)
+        for (int k = 0; k < n_temps; ++k)
+            if (populations[k] < 1 || populations[k] > R) return NULL;
     if (D < 2 || D > 3 || L < 2 || (L & 1) || R < 1 || n_temps < 1 || n_sweeps < 0) return NULL;
     if (kind != OR_PM1 && kind != OR_REAL) return NULL;
     if (betas[0] != 0.0) return NULL;
@@ -352,6 +378,9 @@ or_sim* or_create(int D, int L, int kind, const float* J, const float* h, int R,
     or_sim* s = (or_sim*)calloc(1, sizeof(or_sim));
     int N = ipow(L, D);
     s->D = D; s->L = L; s->N = N; s->kind = kind; s->R = R; s->G = (R + 63) / 64;
+    s->Rcap = R; s->R_src_last = R;
+    s->Rk = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_temps);
+    for (int k = 0; k < n_temps; ++k) s->Rk[k] = populations ? populations[k] : R;
     s->n_temps = n_temps; s->n_sweeps = n_sweeps; s->k_next = 0; s->acc_grad = accumulate_grad;
     s->seed = seed; s->inst = rng_instance; s->tag = rng_tag;
     s->J = (float*)malloc(sizeof(float) * (size_t)D * N);
@@ -404,7 +433,7 @@ void or_destroy(or_sim* s)
     free(s->J); free(s->h); free(s->betas); free(s->nbr); free(s->bond);
     free(s->s); free(s->tmp); free(s->E); free(s->parent); free(s->family);
     free(s->family_tmp); free(s->counts); free(s->w); free(s->P); free(s->obs);
-    free(s->cJ); free(s->ch);
+    free(s->cJ); free(s->ch); free(s->Rk);
     free(s);
 }
 
@@ -471,11 +500,15 @@ int or_step(or_sim* s)
     if (k >= s->n_temps) return -1;
     double lnQ = 0.0;
     if (k == 0) {
+        s->R = s->Rk[0];
         init_spins(s->N, s->R, s->seed, s->inst, s->tag, s->s);
         for (int r = 0; r < s->R; ++r) s->family[r] = s->parent[r] = r;
     } else {
-        resample_core(s->kind, s->R, s->E, s->betas[k - 1], s->betas[k], k, s->seed, s->inst,
-                      s->tag, s->w, s->P, s->parent, s->counts, &lnQ, NULL);
+        const int Rn = s->Rk[k];
+        resample_core2(s->kind, s->R, Rn, s->E, s->betas[k - 1], s->betas[k], k, s->seed, s->inst,
+                       s->tag, s->w, s->P, s->parent, s->counts, &lnQ, NULL);
+        s->R_src_last = s->R;
+        s->R = Rn;
         for (int j = 0; j < s->R; ++j) {
             memcpy(s->tmp + (size_t)j * s->N, s->s + (size_t)s->parent[j] * s->N, (size_t)s->N);
             s->family_tmp[j] = s->family[s->parent[j]];
@@ -509,9 +542,11 @@ void or_get_parents(const or_sim* s, int32_t* out) { memcpy(out, s->parent, size
 void or_get_family(const or_sim* s, int32_t* out) { memcpy(out, s->family, sizeof(int32_t) * (size_t)s->R); }
 void or_get_weights(const or_sim* s, double* w, double* P)
 {
-    memcpy(w, s->w, sizeof(double) * (size_t)s->R);
-    memcpy(P, s->P, sizeof(double) * (size_t)s->R);
+    memcpy(w, s->w, sizeof(double) * (size_t)s->R_src_last);
+    memcpy(P, s->P, sizeof(double) * (size_t)s->R_src_last);
 }
+
+int or_current_R(const or_sim* s) { return s->R; }
 void or_get_obs(const or_sim* s, int k, double* out) { memcpy(out, s->obs + (size_t)k * 8, 8 * sizeof(double)); }
 void or_get_grad_counts(const or_sim* s, int64_t* cJ, int64_t* ch)
 {

@@ -420,3 +420,54 @@ def test_overlap(oracle):
     np.testing.assert_array_equal(hist, np.bincount((q + N) // 2, minlength=N + 1))
     assert oracle.overlap(N, sa, sa)[N] == R
     assert oracle.overlap(N, sa, -sa)[0] == R
+
+
+def _dps(betas, R0, beta_max):
+    from paper_1710_09025_gb300 import schedules as S
+    return np.maximum(1, np.rint(S.dps_population(betas, R0, beta_max))).astype(np.int32)
+
+
+def test_dynamic_population_follows_schedule(oracle):
+    D, L = 3, 4
+    J = W.couplings_pm(D, L, 301)
+    betas = W.schedule_lb(21, 5.0)
+    pops = _dps(betas, 400, 5.0)
+    assert pops[0] == 400 and pops[-1] < 20
+    s = oracle.Sim(D, L, PM1, J, None, int(pops.max()), betas, 3, 17, populations=pops)
+    for k in range(len(betas)):
+        s.step()
+        assert s.R_now == pops[k]
+        assert s.spins().shape[0] == pops[k]
+        fam = s.family()
+        assert np.all(np.diff(fam) >= 0)
+        if k > 0:
+            par = s.parents()
+            assert len(par) == pops[k] and np.all(np.diff(par) >= 0) and par.max() < pops[k - 1]
+        np.testing.assert_array_equal(np.array(s.energies()), _energy_pm(D, L, J, s.spins()))
+        assert s.obs(k)["R"] == pops[k]
+
+
+@pytest.mark.parametrize("case", ["pm_3d_L2", "real_2d_L4_field"])
+def test_dynamic_population_matches_exact(oracle, case):
+    if case == "pm_3d_L2":
+        D, L, kind = 3, 2, PM1
+        J, h = W.couplings_pm(D, L, 311), None
+        betas = W.schedule_lb(11, 2.0)
+    else:
+        D, L, kind = 2, 4, REAL
+        J, h = W.couplings_pm(D, L, 312), W.field_uniform(16, 313)
+        betas = W.schedule_lb(11, 1.5)
+    ex = oracle.exact(D, L, J.astype(np.float64), None if h is None else h.astype(np.float64), betas)
+    pops = np.maximum(200, _dps(betas, 2400, float(betas[-1]))).astype(np.int32)
+    recs = []
+    for sd in range(3000, 3016):
+        s = oracle.Sim(D, L, kind, J, h, int(pops.max()), betas, 6, sd, populations=pops)
+        s.run()
+        o = [s.obs(k) for k in range(len(betas))]
+        recs.append(dict(E=np.array([x["E_mean"] for x in o]), bF=np.array([x["betaF"] for x in o]),
+                         lnQsum=np.cumsum([x["lnQ"] for x in o])))
+    for k in (3, 6, 10):
+        assert _z([r["E"][k] for r in recs], ex["E"][k]) < 5
+        assert _z([r["bF"][k] for r in recs], ex["betaF"][k]) < 5
+        ratio = math.exp(ex["lnZ"][k] - ex["lnZ"][0])
+        assert _z([math.exp(r["lnQsum"][k]) / ratio for r in recs], 1.0) < 5
