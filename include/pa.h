@@ -62,6 +62,10 @@ typedef struct {
     uint32_t rng_tag;        /* 4-bit tag: independent populations (overlap)           */
     int32_t threads;         /* 0 = tuned default; else threads per block              */
     int32_t groups_per_block;/* 0 = tuned default (packed layout)                      */
+    /* dynamic population (Sec. III.D, Eq. 6): host array of n_temps replica
+     * counts, 1 <= populations[k] <= R (R is then the capacity); resampling into
+     * temperature k draws populations[k] copies.  NULL keeps R throughout. */
+    const int32_t* populations;
 } pa_options;
 
 /* Per-temperature observables (Sec. II.B, Eq. 2-3; Sec. V.A, Eq. 9). */
@@ -145,7 +149,9 @@ int pa_grad(pa_ctx* ctx, const double* gbar, double* dJ, double* dh);
  * (N + sum_i S^a_i S^b_i) / 2. */
 int pa_overlap(pa_ctx* a, pa_ctx* b, int64_t* hist);
 
-/* Copies of the current state to host memory (synchronise). */
+/* Copies of the current state to host memory (synchronise).  With a dynamic
+ * population the current population is populations[last completed step]
+ * (pa_sizes reports it as R). */
 int pa_get_spins(pa_ctx* ctx, int8_t* host_spins /* R*N, +1/-1, replica-major */);
 /* Replicas [r0, r0 + n) only (0 <= r0, r0 + n <= R): n*N bytes, +1/-1. */
 int pa_get_spins_range(pa_ctx* ctx, int r0, int n, int8_t* host_spins);

@@ -38,7 +38,8 @@ class PAError(RuntimeError):
 class pa_options(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int32), ("accumulate_grad", ctypes.c_int32),
                 ("rng_instance", ctypes.c_uint32), ("rng_tag", ctypes.c_uint32),
-                ("threads", ctypes.c_int32), ("groups_per_block", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("groups_per_block", ctypes.c_int32),
+                ("populations", ctypes.c_void_p)]
 
 
 class pa_inst_desc(ctypes.Structure):
@@ -135,10 +136,22 @@ def _current_stream():
 # ---------------- the C entry points, same names ----------------
 
 def pa_options_default(**kw) -> pa_options:
+    """Default options with fields overridden by keyword.  ``populations`` may
+    be a sequence of per-temperature population sizes; the int32 copy is kept
+    on the returned struct (pa_create copies it, so it need only outlive that
+    call)."""
     o = pa_options()
     _check(load().pa_options_default(ctypes.byref(o)))
     for k, v in kw.items():
-        setattr(o, k, v)
+        if k == "populations":
+            if v is None:
+                o.populations = None
+                continue
+            arr = np.ascontiguousarray(v, dtype=np.int32)
+            o._populations = arr
+            o.populations = arr.ctypes.data
+        else:
+            setattr(o, k, v)
     return o
 
 

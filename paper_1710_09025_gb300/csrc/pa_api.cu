@@ -29,6 +29,7 @@ struct pa_ctx {
     int gpb, threads, real_warps;
     double betaF0, log_R;
     std::vector<double> betas;
+    std::vector<int> Rk;        // population at each temperature (R = capacity)
     std::vector<float> Jh, hh;  // flushed host copies
     // device
     void* ws;
@@ -56,6 +57,7 @@ struct pa_ctx {
     unsigned long long* hist;
     double *gbar_d, *dJ_d, *dh_d;
     pa::ObsPartial* obspart;
+    double* Rk_d;               // populations as doubles (gradient normalisation)
     cudaGraphExec_t gexec;
     std::string err;
     // profiling: event pairs per phase, launch counter
@@ -129,7 +131,7 @@ struct Layout {
 enum {
     W_J, W_H, W_JNEG, W_JFIX, W_HFIX, W_BETAS, W_S0, W_S1, W_E32, W_E128, W_PARENT, W_FAM0, W_FAM1,
     W_COUNTS, W_BLOCKSUM, W_W, W_P, W_TOT, W_T, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
-    W_DH, W_OBSPART, W_COUNT
+    W_DH, W_OBSPART, W_RK, W_COUNT
 };
 
 static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps, int acc_grad)
@@ -168,6 +170,7 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
     sz[W_DJ] = acc_grad ? sizeof(double) * D * N : 0;
     sz[W_DH] = acc_grad ? sizeof(double) * N : 0;
     sz[W_OBSPART] = sizeof(pa::ObsPartial) * pa::kObsBlocks;
+    sz[W_RK] = sizeof(double) * n_temps;
     Layout lay;
     size_t off = 0;
     for (int i = 0; i < W_COUNT; ++i) {
@@ -224,6 +227,12 @@ static int validate(std::string& err, int D, int L, int kind, const float* J, co
         if (o->accumulate_grad && kind != PA_REAL) { err = "accumulate_grad needs PA_REAL"; return PA_EINVAL; }
         if (o->rng_instance >= (1u << 24)) { err = "rng_instance must be < 2^24"; return PA_EINVAL; }
         if (o->rng_tag >= 16u) { err = "rng_tag must be < 16"; return PA_EINVAL; }
+        if (o->populations)
+            for (int k = 0; k < n_temps; ++k)
+                if (o->populations[k] < 1 || o->populations[k] > R) {
+                    err = "populations[k] must be in [1, R]";
+                    return PA_EINVAL;
+                }
     }
     return PA_OK;
 }
@@ -276,6 +285,8 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->seed = seed; c->inst = o.rng_instance; c->tag = o.rng_tag; c->acc_grad = o.accumulate_grad ? 1 : 0;
     c->st = (cudaStream_t)stream;
     c->betas.assign(betas, betas + n_temps);
+    c->Rk.assign(n_temps, R);
+    if (o.populations) c->Rk.assign(o.populations, o.populations + n_temps);
     c->betaF0 = -(double)c->N * std::log(2.0);
     c->log_R = std::log((double)R);
     c->gexec = nullptr;
@@ -346,6 +357,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->dJ_d = c->acc_grad ? (double*)at(W_DJ) : nullptr;
     c->dh_d = c->acc_grad ? (double*)at(W_DH) : nullptr;
     c->obspart = (pa::ObsPartial*)at(W_OBSPART);
+    c->Rk_d = (double*)at(W_RK);
 
     // couplings: sign masks (+-J), fixed-point copies (real)
     std::vector<uint8_t> jn(N, 0);
@@ -381,6 +393,8 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
         up(c->hfix, hf.data(), sizeof(longlong2) * N);
     }
     up(c->betas_d, c->betas.data(), sizeof(double) * n_temps);
+    std::vector<double> rkd(c->Rk.begin(), c->Rk.end());
+    up(c->Rk_d, rkd.data(), sizeof(double) * n_temps);
     if (rc2 == PA_OK) {
         cudaError_t e = cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * (size_t)R, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(StepAcc) * n_temps, c->st);
@@ -469,27 +483,29 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
 {
     const int k = c->k_next;
     const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
-    const int R = c->R;
+    const int R = c->Rk[k];                      // population after this step
+    const int G = (R + 63) / 64;
     const double beta = c->betas[k];
     std::memset(pl, 0, sizeof *pl);
     pl->k = k;
     if (k > 0) {
         pa::ResampleArgs& ra = pl->rs;
-        ra.R = R; ra.kind = c->kind == PA_PM1 ? 0 : 1;
+        const int Rprev = c->Rk[k - 1];
+        ra.R = Rprev; ra.Rn = R; ra.kind = c->kind == PA_PM1 ? 0 : 1;
         ra.E32 = c->E32; ra.E128 = c->E128;
         ra.prev = c->acc + (k - 1); ra.cur = c->acc + k;
         ra.w = c->w; ra.P = c->P; ra.tot = c->tot; ra.T = c->T;
         ra.counts = c->counts; ra.blocksum = c->blocksum; ra.parent = c->parent;
         ra.fam_in = c->fam[c->famcur]; ra.fam_out = c->fam[c->famcur ^ 1];
         ra.dbeta = c->betas[k] - c->betas[k - 1];
-        ra.log_R = c->log_R; ra.betaF0 = c->betaF0; ra.k = k;
+        ra.log_R = std::log((double)Rprev); ra.betaF0 = c->betaF0; ra.k = k;
         ra.key0 = k0; ra.key1 = k1; ra.c3 = pa::counter3(pa::STREAM_RES, c->tag, c->inst);
         c->famcur ^= 1;
     }
     if (c->kind == PA_PM1) {
         fill_packed_step(&pl->pk.s, c->D, beta, k, c->n_sweeps, k0, k1);
         pa::PackedInst& in = pl->pk.i;
-        in.jneg = c->jneg; in.E = c->E32; in.G = c->G; in.R = R; in.NP = c->NP;
+        in.jneg = c->jneg; in.E = c->E32; in.G = G; in.R = R; in.NP = c->NP;
         in.c3 = pa::counter3(pa::STREAM_PLANE, c->tag, c->inst);
         if (c->layout == PA_LAYOUT_PACKED) {
             // k > 0: the replica gather is fused into the sweep's tile load
@@ -529,12 +545,13 @@ static int enqueue_init(pa_ctx* c)
 {
     const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
     const uint32_t c3 = pa::counter3(pa::STREAM_INIT, c->tag, c->inst);
+    const int R0 = c->Rk[0];
     if (c->layout == PA_LAYOUT_PACKED)
-        PA_CK(c, pa::launch_init_packed(c->S[c->cur], c->N, c->G, k0, k1, c3, c->st));
+        PA_CK(c, pa::launch_init_packed(c->S[c->cur], c->N, (R0 + 63) / 64, k0, k1, c3, c->st));
     else
-        PA_CK(c, pa::launch_init_i8(c->S8[c->cur], c->N, c->NP, c->R, k0, k1, c3, c->st));
+        PA_CK(c, pa::launch_init_i8(c->S8[c->cur], c->N, c->NP, R0, k0, k1, c3, c->st));
     iota_kernel<<<(c->R + 255) / 256, 256, 0, c->st>>>(c->fam[c->famcur], c->parent, c->R);
-    acc0_kernel<<<1, 1, 0, c->st>>>(c->acc, c->betaF0, c->R);
+    acc0_kernel<<<1, 1, 0, c->st>>>(c->acc, c->betaF0, R0);
     PA_CK(c, cudaGetLastError());
     c->launches += 3;
     return PA_OK;
@@ -644,7 +661,7 @@ extern "C" int pa_observables(pa_ctx* c, int k, pa_obs* out)
     StepAcc a;
     PA_CK(c, cudaMemcpyAsync(&a, c->acc + k, sizeof a, cudaMemcpyDeviceToHost, c->st));
     PA_CK(c, cudaStreamSynchronize(c->st));
-    const double R = (double)c->R;
+    const double R = (double)c->Rk[k];
     double Em, E2m;
     if (c->kind == PA_PM1) {
         Em = (double)a.sumE / R;
@@ -659,9 +676,9 @@ extern "C" int pa_observables(pa_ctx* c, int k, pa_obs* out)
     out->C = beta * beta * (E2m - Em * Em) / c->N;
     out->lnQ = a.lnQ;
     out->betaF = a.betaF;
-    out->S_f = c->log_R - a.sum_clnc / R;
+    out->S_f = std::log(R) - a.sum_clnc / R;
     out->rho_s = R / std::exp(out->S_f);
-    out->R = c->R;
+    out->R = c->Rk[k];
     return PA_OK;
 }
 
@@ -683,7 +700,7 @@ extern "C" int pa_grad(pa_ctx* c, const double* gbar, double* dJ, double* dh)
         if (gbar[k] != 0.0) { c->err = "gbar weights a step that has not run"; return PA_ESTATE; }
     const int nJ = c->D * c->N;
     PA_CK(c, cudaMemcpyAsync(c->gbar_d, gbar, sizeof(double) * c->n_temps, cudaMemcpyHostToDevice, c->st));
-    PA_CK(c, pa::launch_grad_backward(c->cJ, c->ch, c->gbar_d, c->betas_d, c->n_temps, nJ, c->N, c->R,
+    PA_CK(c, pa::launch_grad_backward(c->cJ, c->ch, c->gbar_d, c->betas_d, c->Rk_d, c->n_temps, nJ, c->N,
                                       c->dJ_d, c->dh_d, c->st));
     PA_CK(c, cudaMemcpyAsync(dJ, c->dJ_d, sizeof(double) * nJ, cudaMemcpyDeviceToHost, c->st));
     if (dh) PA_CK(c, cudaMemcpyAsync(dh, c->dh_d, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
@@ -691,19 +708,22 @@ extern "C" int pa_grad(pa_ctx* c, const double* gbar, double* dJ, double* dh)
     return PA_OK;
 }
 
+// population after the last completed step (before any step: the initial one)
+static int pop_now(const pa_ctx* c) { return c->Rk[c->k_next > 0 ? c->k_next - 1 : 0]; }
+
 extern "C" int pa_overlap(pa_ctx* a, pa_ctx* b, int64_t* hist)
 {
     if (!a || !b || !hist) return PA_EINVAL;
-    if (a->D != b->D || a->L != b->L || a->R != b->R || a->layout != b->layout) {
+    if (a->D != b->D || a->L != b->L || pop_now(a) != pop_now(b) || a->layout != b->layout) {
         a->err = "overlap needs two contexts of the same lattice, R and layout";
         return PA_EINVAL;
     }
     PA_CK(a, cudaStreamSynchronize(b->st));
     PA_CK(a, cudaMemsetAsync(a->hist, 0, sizeof(unsigned long long) * (a->N + 1), a->st));
     if (a->layout == PA_LAYOUT_PACKED)
-        PA_CK(a, pa::launch_overlap_packed(a->S[a->cur], b->S[b->cur], a->N, a->R, a->hist, a->st));
+        PA_CK(a, pa::launch_overlap_packed(a->S[a->cur], b->S[b->cur], a->N, pop_now(a), a->hist, a->st));
     else
-        PA_CK(a, pa::launch_overlap_i8(a->S8[a->cur], b->S8[b->cur], a->N, a->NP, a->R, a->hist, a->st));
+        PA_CK(a, pa::launch_overlap_i8(a->S8[a->cur], b->S8[b->cur], a->N, a->NP, pop_now(a), a->hist, a->st));
     PA_CK(a, cudaMemcpyAsync(hist, a->hist, sizeof(int64_t) * (a->N + 1), cudaMemcpyDeviceToHost, a->st));
     PA_CK(a, cudaStreamSynchronize(a->st));
     return PA_OK;
@@ -711,7 +731,7 @@ extern "C" int pa_overlap(pa_ctx* a, pa_ctx* b, int64_t* hist)
 
 extern "C" int pa_get_spins_range(pa_ctx* c, int r0, int n, int8_t* dst)
 {
-    if (!c || !dst || r0 < 0 || n < 0 || r0 + n > c->R) return PA_EINVAL;
+    if (!c || !dst || r0 < 0 || n < 0 || r0 + n > pop_now(c)) return PA_EINVAL;
     if (n == 0) return PA_OK;
     if (c->layout == PA_LAYOUT_PACKED) {
         PA_CK(c, pa::launch_unpack_packed(c->S[c->cur], c->tmp8, c->N, r0, n, c->st));
@@ -727,19 +747,20 @@ extern "C" int pa_get_spins_range(pa_ctx* c, int r0, int n, int8_t* dst)
 extern "C" int pa_get_spins(pa_ctx* c, int8_t* dst)
 {
     if (!c) return PA_EINVAL;
-    return pa_get_spins_range(c, 0, c->R, dst);
+    return pa_get_spins_range(c, 0, pop_now(c), dst);
 }
 
 extern "C" int pa_get_energies(pa_ctx* c, int64_t* dst)
 {
     if (!c || !dst) return PA_EINVAL;
+    const int Rn = pop_now(c);
     if (c->kind == PA_PM1) {
-        std::vector<int32_t> e(c->R);
-        PA_CK(c, cudaMemcpyAsync(e.data(), c->E32, sizeof(int32_t) * c->R, cudaMemcpyDeviceToHost, c->st));
+        std::vector<int32_t> e(Rn);
+        PA_CK(c, cudaMemcpyAsync(e.data(), c->E32, sizeof(int32_t) * Rn, cudaMemcpyDeviceToHost, c->st));
         PA_CK(c, cudaStreamSynchronize(c->st));
-        for (int r = 0; r < c->R; ++r) dst[r] = e[r];
+        for (int r = 0; r < Rn; ++r) dst[r] = e[r];
     } else {
-        PA_CK(c, cudaMemcpyAsync(dst, c->E128, sizeof(longlong2) * c->R, cudaMemcpyDeviceToHost, c->st));
+        PA_CK(c, cudaMemcpyAsync(dst, c->E128, sizeof(longlong2) * Rn, cudaMemcpyDeviceToHost, c->st));
         PA_CK(c, cudaStreamSynchronize(c->st));
     }
     return PA_OK;
@@ -748,7 +769,7 @@ extern "C" int pa_get_energies(pa_ctx* c, int64_t* dst)
 extern "C" int pa_get_parents(pa_ctx* c, int32_t* dst)
 {
     if (!c || !dst) return PA_EINVAL;
-    PA_CK(c, cudaMemcpyAsync(dst, c->parent, sizeof(int32_t) * c->R, cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaMemcpyAsync(dst, c->parent, sizeof(int32_t) * pop_now(c), cudaMemcpyDeviceToHost, c->st));
     PA_CK(c, cudaStreamSynchronize(c->st));
     return PA_OK;
 }
@@ -756,7 +777,7 @@ extern "C" int pa_get_parents(pa_ctx* c, int32_t* dst)
 extern "C" int pa_get_family(pa_ctx* c, int32_t* dst)
 {
     if (!c || !dst) return PA_EINVAL;
-    PA_CK(c, cudaMemcpyAsync(dst, c->fam[c->famcur], sizeof(int32_t) * c->R, cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaMemcpyAsync(dst, c->fam[c->famcur], sizeof(int32_t) * pop_now(c), cudaMemcpyDeviceToHost, c->st));
     PA_CK(c, cudaStreamSynchronize(c->st));
     return PA_OK;
 }
@@ -777,7 +798,7 @@ extern "C" int pa_sizes(const pa_ctx* c, int* D, int* L, int* N, int* R, int* n_
     if (D) *D = c->D;
     if (L) *L = c->L;
     if (N) *N = c->N;
-    if (R) *R = c->R;
+    if (R) *R = pop_now(c);
     if (n_temps) *n_temps = c->n_temps;
     if (layout) *layout = c->layout;
     return PA_OK;
@@ -911,8 +932,8 @@ extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_
     *out = nullptr;
     if (D != 3) { g_create_err = "batched sweeps support D = 3"; return PA_EINVAL; }
     if (n_inst < 1 || !descs) { g_create_err = "need at least one instance"; return PA_EINVAL; }
-    if (opt && (opt->layout != PA_LAYOUT_AUTO || opt->accumulate_grad)) {
-        g_create_err = "batch: layout must be AUTO and accumulate_grad 0";
+    if (opt && (opt->layout != PA_LAYOUT_AUTO || opt->accumulate_grad || opt->populations)) {
+        g_create_err = "batch: layout must be AUTO, accumulate_grad 0 and populations NULL";
         return PA_EINVAL;
     }
     pa_batch* b = new pa_batch();

@@ -107,7 +107,8 @@ cudaError_t launch_sweep_batched(const PackedStep& ps, const RealStep& rs, const
 
 // ---------------- resampling and observables ----------------
 struct ResampleArgs {
-    int R, kind;                 // kind 0: E32, 1: E128
+    int R, kind;                 // R: source replicas; kind 0: E32, 1: E128
+    int Rn;                      // copies drawn (the new population)
     const int32_t* E32;
     const longlong2* E128;
     const StepAcc* prev;         // acc[k-1]: E_min, sum_lnQ
@@ -147,8 +148,8 @@ struct ObsArgs {
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st);
 cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, cudaStream_t st);
 cudaError_t launch_grad_backward(const unsigned long long* cJ, const unsigned long long* ch,
-                                 const double* gbar, const double* betas, int n_temps, int nJ,
-                                 int N, int R, double* dJ, double* dh, cudaStream_t st);
+                                 const double* gbar, const double* betas, const double* Rk,
+                                 int n_temps, int nJ, int N, double* dJ, double* dh, cudaStream_t st);
 
 // message returned by pa_last_error(NULL) for calls without a context
 void set_global_error(const char* msg);

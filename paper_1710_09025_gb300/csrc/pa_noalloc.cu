@@ -132,6 +132,7 @@ extern "C" int pa_resample_static(const int32_t* d_E, int R, double beta_prev, d
     static_prep_kernel<<<1, 1024, 0, st>>>(d_E, R, base);
     pa::ResampleArgs ra;
     ra.R = R;
+    ra.Rn = R;
     ra.kind = 0;
     ra.E32 = d_E;
     ra.E128 = nullptr;

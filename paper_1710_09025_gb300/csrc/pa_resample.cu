@@ -107,7 +107,7 @@ __global__ void rs_finalize_batched(const ResampleArgs* tab)
 
 __device__ __forceinline__ void rs_draws_body(const ResampleArgs& a, int q)
 {
-    if (q >= a.R) return;
+    if (q >= a.Rn) return;
     const int nchunks = (a.R + kChunk - 1) / kChunk;
     const u32x4 o = philox((uint32_t)q, (uint32_t)a.k, 0u, a.c3, a.key0, a.key1);
     const double S = a.T[nchunks];
@@ -242,7 +242,7 @@ cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
     rs_weights_kernel<<<nchunks, 256, 0, st>>>(a);
     rs_offsets_kernel<<<1, 32, 0, st>>>(a);
     rs_finalize_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
-    rs_draws_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
+    rs_draws_kernel<<<(a.Rn + 255) / 256, 256, 0, st>>>(a);
     rs_blocksum_kernel<<<nb, 1024, 0, st>>>(a.counts, a.R, a.blocksum);
     rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a.blocksum, nb);
     rs_fill_kernel<<<nb, 1024, 0, st>>>(a);
@@ -389,8 +389,8 @@ cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, cudaStream_t 
 // d(beta F)/dJ_b = -beta <S_i S_j>, d(beta F)/dh_i = -beta <S_i> (from Eq. 1),
 // estimated with the exact population sums after the sweeps at beta_k.
 __global__ void grad_backward_kernel(const unsigned long long* cJ, const unsigned long long* ch,
-                                     const double* gbar, const double* betas, int n_temps, int nJ,
-                                     int N, int R, double* dJ, double* dh)
+                                     const double* gbar, const double* betas, const double* Rk,
+                                     int n_temps, int nJ, int N, double* dJ, double* dh)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nJ + N) return;
@@ -399,20 +399,19 @@ __global__ void grad_backward_kernel(const unsigned long long* cJ, const unsigne
     const int stride = isJ ? nJ : N;
     const unsigned long long* c = isJ ? cJ : ch;
     double acc = 0.0;
-    const double invR = (double)R;
     for (int k = 0; k < n_temps; ++k) {
-        const double m = __ddiv_rn((double)(long long)c[(size_t)k * stride + idx], invR);
+        const double m = __ddiv_rn((double)(long long)c[(size_t)k * stride + idx], Rk[k]);
         acc = __dadd_rn(acc, __dmul_rn(gbar[k], -__dmul_rn(betas[k], m)));
     }
     if (isJ) dJ[idx] = acc; else dh[idx] = acc;
 }
 
 cudaError_t launch_grad_backward(const unsigned long long* cJ, const unsigned long long* ch,
-                                 const double* gbar, const double* betas, int n_temps, int nJ,
-                                 int N, int R, double* dJ, double* dh, cudaStream_t st)
+                                 const double* gbar, const double* betas, const double* Rk,
+                                 int n_temps, int nJ, int N, double* dJ, double* dh, cudaStream_t st)
 {
     const int n = nJ + N;
-    grad_backward_kernel<<<(n + 255) / 256, 256, 0, st>>>(cJ, ch, gbar, betas, n_temps, nJ, N, R, dJ, dh);
+    grad_backward_kernel<<<(n + 255) / 256, 256, 0, st>>>(cJ, ch, gbar, betas, Rk, n_temps, nJ, N, dJ, dh);
     return cudaGetLastError();
 }
 

@@ -33,11 +33,12 @@ def _assert_obs(o, r, kind):
 
 
 def run_parity(pa, oracle, D, L, kind, J, h, R, betas, ns, seed, layout=0, inst=0, tag=0,
-               grad=False, graph_every=None, shape=None):
+               grad=False, graph_every=None, shape=None, populations=None):
     P = pa
     ref = oracle.Sim(D, L, kind, J, h, R, betas, ns, seed, rng_instance=inst, rng_tag=tag,
-                     accumulate_grad=grad)
-    opts = dict(layout=layout, rng_instance=inst, rng_tag=tag, accumulate_grad=int(grad))
+                     accumulate_grad=grad, populations=populations)
+    opts = dict(layout=layout, rng_instance=inst, rng_tag=tag, accumulate_grad=int(grad),
+                populations=populations)
     if shape:
         opts.update(groups_per_block=shape[0], threads=shape[1])
     pop = P.Population(D, L, kind, J, h, R, betas, ns, seed, **opts)
