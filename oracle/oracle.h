@@ -92,10 +92,6 @@ void or_get_grad_counts(const or_sim* s, int64_t* cJ, int64_t* ch); /* n_temps*D
 int or_sweeps_groups(int D, int L, int kind, const float* J, const float* h,
                      double beta, int k, int n_sweeps, uint64_t seed, uint32_t inst,
                      uint32_t tag, int g0, int ng, int R, int8_t* state);
-/* the +-J low-temperature rule alone (only dE = 4 accepted, thr < 2^16): n_cand
- * lanes decided in order from the 2048-bit stream `words` (64 words, bit p =
- * bit p%32 of words[p/32]); flips[c] = 1 if lane c flips; returns the bits read */
-int or_lowt_run(const uint32_t* words, int n_cand, uint64_t thr, uint8_t* flips);
 /* resampling of R replicas with energies E (int128 as lo/hi pairs) from
  * beta_prev to beta_next at step k; outputs w, P, parent, counts and lnQ. */
 int or_resample(int kind, int R, const int64_t* E, double beta_prev, double beta_next, int k,

@@ -84,7 +84,6 @@ def lib():
                 "or_get_grad_counts": (None, [vp, vp, vp]),
                 "or_sweeps_groups": (i32, [i32, i32, i32, vp, vp, dbl, i32, i32, u64, u32, u32,
                                            i32, i32, i32, vp]),
-                "or_lowt_run": (i32, [vp, i32, u64, vp]),
                 "or_resample": (i32, [i32, i32, vp, dbl, dbl, i32, u64, u32, u32, vp, vp, vp, vp,
                                       vp, vp]),
                 "or_energies": (None, [i32, i32, i32, vp, vp, i32, vp, vp]),
@@ -195,15 +194,6 @@ def sweeps_groups(D, L, kind, J, h, beta, k, n_sweeps, seed, inst, tag, g0, ng, 
     lib().or_sweeps_groups(D, L, kind, _p(J), _p(h), beta, k, n_sweeps, seed, inst, tag, g0, ng,
                            R, _p(state))
     return state
-
-
-def lowt_run(words, n_cand, thr):
-    """+-J low-temperature rule on one 2048-bit stream: (flips[n_cand], bits read)."""
-    words = np.ascontiguousarray(words, dtype=np.uint32)
-    assert words.shape == (64,) and 0 <= n_cand <= 64
-    flips = np.zeros(max(n_cand, 1), np.uint8)
-    pos = lib().or_lowt_run(_p(words), n_cand, int(thr), _p(flips))
-    return flips[:n_cand].astype(bool), pos
 
 
 def overlap(N, a, b):

@@ -34,14 +34,6 @@
  *            group g: 16 calls with counter (q, hs, 16g+m, c3), m = 0..15,
  *            give 32 planes, plane 2m = out0|out1<<32, plane 2m+1 = out2|out3<<32;
  *            replica 64g+j draws r = sum_b bit_j(plane_b) 2^(31-b).
- *            Low-temperature rule (only dE = 4 can be accepted: thr(8) = 0,
- *            0 < thr(4) < 2^32, hence thr(4) < 2^16): the same 16 calls read
- *            as one bit stream B (bit p = bit p%32 of out[(p/32)%4] of call
- *            p/128); the dE = 4 lanes of the word, in ascending j, each read
- *            r MSB first from B at a cursor, r = sum_t B[pos+t] 2^(31-t).
- *            The cursor passes the first 1 among the top 16 bits of r (that
- *            bit alone gives r >= 2^16 > thr, a rejection), else all 32 bits
- *            (then accept iff r < thr).
  *   WORD   : (real couplings) r(rho, hs, q) = out[q&3] of counter (q>>2, hs, rho, c3).
  *   RESAMPLE: draw q at step k: counter (q, k, 0, c3), u = 53-bit uniform.
  */
@@ -149,39 +141,11 @@ typedef struct {
 /* +-J couplings: the energy change of flipping S_i is dE = 2 S_i sum_nb J S_nb
  * = 4D - 4 n_unsat, n_unsat = number of the 2D bonds of i with J S_i S_nb = -1.
  * Accept iff dE <= 0 or r < floor(exp(-beta dE) 2^32). */
-/* bit p of the low-temperature stream of one word (16 calls, 2048 bits) */
-static int stream_bit(const uint32_t* words, int p) { return (int)((words[p >> 5] >> (p & 31)) & 1u); }
-
-/* one dE = 4 lane under the low-temperature rule (thr < 2^16): r is read MSB
- * first at the cursor; a 1 among its top 16 bits rejects and the cursor
- * passes it, otherwise the cursor passes all 32 bits and r < thr decides */
-static int lowt_decide(const uint32_t* words, int* pos, uint64_t thr)
-{
-    for (int t = 0; t < 16; ++t)
-        if (stream_bit(words, *pos + t)) {
-            *pos += t + 1;
-            return 0;
-        }
-    uint64_t r = 0;
-    for (int t = 0; t < 32; ++t) r = (r << 1) | (uint64_t)stream_bit(words, *pos + t);
-    *pos += 32;
-    return r < thr;
-}
-
-int or_lowt_run(const uint32_t* words, int n_cand, uint64_t thr, uint8_t* flips)
-{
-    int pos = 0;
-    for (int c = 0; c < n_cand; ++c) flips[c] = (uint8_t)lowt_decide(words, &pos, thr);
-    return pos;
-}
-
 static void halfsweep_pm(const lat_ctx* c, int8_t* s, int r0, int nrep, double beta, int hs,
                          int parity)
 {
     uint64_t thr[4];
     for (int n = 1; n <= 3; ++n) thr[n] = or_threshold_pm(beta, 4 * n);
-    /* only dE = 4 can be accepted, with thr(4) < 2^16 since thr(8) = 0 */
-    const int low_t = thr[1] > 0 && thr[1] < 4294967296ull && thr[2] == 0;
     uint32_t c3 = or_counter3(OR_STREAM_PLANE, c->tag, c->inst);
     int twoD = 2 * c->D;
     for (int rb = 0; rb < nrep; rb += 64) {
@@ -191,8 +155,6 @@ static void halfsweep_pm(const lat_ctx* c, int8_t* s, int r0, int nrep, double b
             uint32_t q = (uint32_t)(i >> 1);
             int have_planes = 0;
             uint64_t planes[32];
-            uint32_t words[64];
-            int pos = 0; /* low-temperature stream cursor */
             for (int j = 0; j < 64 && rb + j < nrep; ++j) {
                 int8_t* sr = s + (size_t)(rb + j) * c->N;
                 int n_unsat = 0;
@@ -211,17 +173,12 @@ static void halfsweep_pm(const lat_ctx* c, int8_t* s, int r0, int nrep, double b
                             or_philox4x32_10(ctr, c->key, out);
                             planes[2 * m] = (uint64_t)out[0] | ((uint64_t)out[1] << 32);
                             planes[2 * m + 1] = (uint64_t)out[2] | ((uint64_t)out[3] << 32);
-                            for (int t = 0; t < 4; ++t) words[4 * m + t] = out[t];
                         }
                         have_planes = 1;
                     }
-                    if (low_t) {
-                        flip = (dE == 4) ? lowt_decide(words, &pos, thr[1]) : 0; /* thr(8), thr(12) = 0 */
-                    } else {
-                        uint64_t r = 0;
-                        for (int b = 0; b < 32; ++b) r |= ((planes[b] >> j) & 1u) << (31 - b);
-                        flip = r < thr[dE / 4];
-                    }
+                    uint64_t r = 0;
+                    for (int b = 0; b < 32; ++b) r |= ((planes[b] >> j) & 1u) << (31 - b);
+                    flip = r < thr[dE / 4];
                 }
                 if (flip) sr[i] = (int8_t)-sr[i];
             }

@@ -471,74 +471,3 @@ def test_dynamic_population_matches_exact(oracle, case):
         assert _z([r["bF"][k] for r in recs], ex["betaF"][k]) < 5
         ratio = math.exp(ex["lnZ"][k] - ex["lnZ"][0])
         assert _z([math.exp(r["lnQsum"][k]) / ratio for r in recs], 1.0) < 5
-
-
-def _lowt_law(p, thr):
-    """Closed forms for one dE = 4 lane under the low-temperature rule when the
-    stream bits are iid with P(1) = p: acceptance probability (16 leading
-    zeros, then the low 16 bits of r, MSB first, below thr) and the mean
-    number of bits the lane reads."""
-    q = 1.0 - p
-    below, prefix = 0.0, 1.0
-    for b in range(15, -1, -1):  # compare v < thr from the most significant bit
-        if (thr >> b) & 1:
-            below += prefix * q      # v has 0 where thr has 1: decided, below
-            prefix *= p
-        else:
-            prefix *= q
-    acc = q ** 16 * below
-    mean_bits = sum((t + 1) * q ** t * p for t in range(16)) + 32 * q ** 16
-    return acc, mean_bits
-
-
-@pytest.mark.parametrize("p,thr", [(0.1, 0x9000), (0.15, 0x2A5), (0.5, 0xFFFF)])
-def test_low_temperature_rule_law(oracle, p, thr):
-    """The low-temperature +-J rule (only dE = 4 can be accepted, thr < 2^16)
-    decides each lane with probability P(r < thr) for r with the stream's bit
-    law, lanes independently (disjoint bits).  Biased streams make acceptance
-    frequent enough to measure; uniform bits (p = 1/2) give thr / 2^32."""
-    rng = np.random.default_rng(int(thr) + int(1000 * p))
-    n_words, n_cand = 12000, 6
-    acc_p, mean_bits = _lowt_law(p, thr)
-    flips = np.zeros((n_words, n_cand), bool)
-    used = np.zeros(n_words)
-    weights = (1 << np.arange(32, dtype=np.uint64)).astype(np.uint64)
-    for w in range(n_words):
-        bits = (rng.random(2048) < p).astype(np.uint64).reshape(64, 32)
-        words = (bits * weights).sum(1).astype(np.uint32)
-        flips[w], used[w] = oracle.lowt_run(words, n_cand, thr)
-    # every lane (rank) accepted with the closed-form probability
-    sd = math.sqrt(acc_p * (1 - acc_p) / n_words) + 1e-12
-    for c in range(n_cand):
-        assert abs(flips[:, c].mean() - acc_p) < 5 * sd + 1e-9, (c, flips[:, c].mean(), acc_p)
-    # consecutive lanes independent: joint acceptance = product
-    joint = (flips[:, :-1] & flips[:, 1:]).mean()
-    sdj = math.sqrt(acc_p ** 2 * (1 - acc_p ** 2) / (n_words * (n_cand - 1))) + 1e-12
-    assert abs(joint - acc_p ** 2) < 6 * sdj + 1e-9, (joint, acc_p ** 2)
-    # bits read: sum of n_cand independent lanes
-    var_bits = sum((t + 1) ** 2 * (1 - p) ** t * p for t in range(16)) + 32 ** 2 * (1 - p) ** 16 \
-        - mean_bits ** 2
-    assert abs(used.mean() - n_cand * mean_bits) < 5 * math.sqrt(n_cand * var_bits / n_words)
-
-
-def test_low_temperature_rule_edges(oracle):
-    zeros = np.zeros(64, np.uint32)
-    ones = np.full(64, 0xFFFFFFFF, np.uint32)
-    # all-zero stream: every lane reads 32 bits, r = 0 < thr
-    f, used = oracle.lowt_run(zeros, 64, 1)
-    assert f.all() and used == 64 * 32
-    # all-one stream: every lane reads one bit and is rejected
-    f, used = oracle.lowt_run(ones, 64, 0xFFFF)
-    assert not f.any() and used == 64
-    # a lane whose 17th bit is its first 1: 16 zeros, then r = 2^15 + ... compared
-    w = np.zeros(64, np.uint32)
-    w[0] = 1 << 16                    # bit 16 of the stream: MSB of the low half
-    f, used = oracle.lowt_run(w, 1, 0x8000)
-    assert not f[0] and used == 32    # r = 0x8000, not below 0x8000
-    f, used = oracle.lowt_run(w, 1, 0x8001)
-    assert f[0] and used == 32
-    # the second lane starts right after the first lane's deciding bit
-    w = np.zeros(64, np.uint32)
-    w[0] = 0b100                      # first 1 at bit 2: lane 0 reads 3 bits
-    f, used = oracle.lowt_run(w, 2, 1)
-    assert list(f) == [False, True] and used == 3 + 32
