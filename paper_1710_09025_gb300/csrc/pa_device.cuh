@@ -77,8 +77,10 @@ __device__ __forceinline__ u32x4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2
 {
 #pragma unroll
     for (int rnd = 0; rnd < 10; ++rnd) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo2 = 0xCD9E8D57u * c2, hi2 = __umulhi(0xCD9E8D57u, c2);
+        // one wide multiply gives both halves of each product
+        const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u, p2 = (uint64_t)c2 * 0xCD9E8D57u;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo2 = (uint32_t)p2, hi2 = (uint32_t)(p2 >> 32);
         const uint32_t n0 = hi2 ^ c1 ^ rk[2 * rnd];
         const uint32_t n2 = hi0 ^ c3 ^ rk[2 * rnd + 1];
         c0 = n0;

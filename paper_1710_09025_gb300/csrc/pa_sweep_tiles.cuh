@@ -42,6 +42,9 @@ __device__ __forceinline__ int site_parity(int i)
     return (x + y + z) & 1;
 }
 
+// a 0 / ~0 32-bit mask widened to 64 bits (both halves the same register)
+__device__ __forceinline__ uint64_t rep32(uint32_t v) { return ((uint64_t)v << 32) | v; }
+
 // One plane of the comparison r < thr for the undecided lanes U.  T (the
 // threshold's bit for each lane's class) is selected by the count bits:
 // n = 0 -> v00, n = 1 -> v01, n = 2 -> v10 (0 / ~0 masks of this plane).
@@ -49,9 +52,7 @@ __device__ __forceinline__ int site_parity(int i)
 __device__ __forceinline__ void plane_step(uint64_t pl, uint32_t v00, uint32_t v01, uint32_t v10,
                                            uint64_t b0, uint64_t b1, uint64_t& U, uint64_t& acc)
 {
-    const uint64_t V00 = (uint64_t)(int64_t)(int32_t)v00;
-    const uint64_t V01 = (uint64_t)(int64_t)(int32_t)v01;
-    const uint64_t V10 = (uint64_t)(int64_t)(int32_t)v10;
+    const uint64_t V00 = rep32(v00), V01 = rep32(v01), V10 = rep32(v10);
     const uint64_t inner = (b0 & V01) | (~b0 & V00);
     const uint64_t T = (b1 & V10) | (~b1 & inner);
     acc |= U & T & ~pl;
@@ -74,8 +75,7 @@ __device__ __forceinline__ void plane_step_uniform(uint64_t pl, uint32_t t, uint
 __device__ __forceinline__ void plane_step_two(uint64_t pl, uint32_t ta, uint32_t tb, uint64_t sel,
                                                uint64_t& U, uint64_t& acc)
 {
-    const uint64_t A = (uint64_t)(int64_t)(int32_t)ta;
-    const uint64_t B = (uint64_t)(int64_t)(int32_t)tb;
+    const uint64_t A = rep32(ta), B = rep32(tb);
     const uint64_t T = (sel & A) | (~sel & B);
     acc |= U & T & ~pl;
     U &= ~(T ^ pl);
@@ -230,33 +230,32 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     const uint32_t m32 = (uint32_t)((int32_t)(jm << (31 - kk)) >> 31);
                     u[kk] = sw0 ^ oth[nb.q[kk]] ^ (((uint64_t)m32 << 32) | m32);
                 }
-                uint64_t m1, m2, m3, b0, b1;
+                // n = b0 + 2 b1 + 4 b2 unsatisfied bonds per lane; dE = 4 (D - n)
+                uint64_t b0, b1, b2, down;
                 if (D == 3) {
                     uint64_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
                     uint64_t s2 = u[3] ^ u[4] ^ u[5], c2 = maj3(u[3], u[4], u[5]);
                     b0 = s1 ^ s2;
                     uint64_t k0 = s1 & s2;
                     b1 = c1 ^ c2 ^ k0;
-                    uint64_t b2 = maj3(c1, c2, k0);
-                    m3 = ~b2 & ~b1 & ~b0;  // n = 0: dE = 12
-                    m2 = ~b2 & ~b1 & b0;   // n = 1: dE = 8
-                    m1 = ~b2 & b1 & ~b0;   // n = 2: dE = 4
+                    b2 = maj3(c1, c2, k0);
+                    down = b2 | (b1 & b0);  // n >= 3: dE <= 0
                 } else {
                     uint64_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
                     b0 = s1 ^ u[3];
                     uint64_t k0 = s1 & u[3];
                     b1 = c1 ^ k0;
-                    uint64_t b2 = c1 & k0;
-                    m3 = 0;
-                    m2 = ~b2 & ~b1 & ~b0;  // n = 0: dE = 8
-                    m1 = ~b2 & ~b1 & b0;   // n = 1: dE = 4
+                    b2 = c1 & k0;
+                    down = b1 | b2;         // n >= 2: dE <= 0
                 }
-                uint64_t acc = ~(m1 | m2 | m3) | (m1 & alw1) | (m2 & alw2) | (m3 & alw3);
+                // in modes 1 and 2 no uphill class is always accepted
+                uint64_t acc = down;
                 const uint32_t g = (uint32_t)(g0 + gl);
                 // MSB-first comparison r < thr over the planes still needed
                 if (s.mode == 1) {
-                    // only dE = 4 lanes are undecided: one threshold, its plane bit is uniform
-                    uint64_t U = m1;
+                    // only dE = 4 lanes (n = D - 1) are undecided: one threshold,
+                    // its plane bit is uniform
+                    uint64_t U = ~down & ((D == 3) ? b1 : b0);
 #pragma unroll
                     for (int m = 0; m < 16; ++m) {
                         if (!U) break;
@@ -268,8 +267,9 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                                            (D == 3) ? s.v10[2 * m + 1] : s.v01[2 * m + 1], U, acc);
                     }
                 } else if (s.mode == 2) {
-                    // dE = 4 and dE = 8 lanes: the threshold bit is picked by one count bit
-                    uint64_t U = m1 | m2;
+                    // dE = 4 and dE = 8 lanes (n = D - 1, D - 2): the threshold bit is
+                    // picked by one count bit
+                    uint64_t U = ~down & ((D == 3) ? (b0 | b1) : ~0ull);
                     const uint64_t sel = (D == 3) ? b1 : b0;  // 1 selects the dE = 4 class
 #pragma unroll
                     for (int m = 0; m < 16; ++m) {
@@ -282,6 +282,17 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                                        (D == 3) ? s.v01[2 * m + 1] : s.v00[2 * m + 1], sel, U, acc);
                     }
                 } else {
+                    uint64_t m1, m2, m3;
+                    if (D == 3) {
+                        m3 = ~b2 & ~b1 & ~b0;  // n = 0: dE = 12
+                        m2 = ~b2 & ~b1 & b0;   // n = 1: dE = 8
+                        m1 = ~b2 & b1 & ~b0;   // n = 2: dE = 4
+                    } else {
+                        m3 = 0;
+                        m2 = ~b2 & ~b1 & ~b0;  // n = 0: dE = 8
+                        m1 = ~b2 & ~b1 & b0;   // n = 1: dE = 4
+                    }
+                    acc |= (m1 & alw1) | (m2 & alw2) | (m3 & alw3);
                     uint64_t U = (m1 & und1) | (m2 & und2) | (m3 & und3);
 #pragma unroll
                     for (int m = 0; m < 16; ++m) {

@@ -49,7 +49,7 @@ def _check_step(P, O, pop, w, J, h, betas, k, seed, groups, E_prev, spins_rows):
 
 
 @pytest.mark.parametrize("name,checks", [("ea3d_L8_pm_R1e5", (1, 2, 120)),
-                                         ("ea3d_L16_pm_R1e6", (1, 150)),
+                                         ("ea3d_L16_pm_R1e6", (1, 150, 250)),
                                          ("ea3d_L6_gauss_R5e4", (1, 60))])
 def test_fullsize_sampled_parity(pa, oracle, name, checks):
     P, O = pa, oracle

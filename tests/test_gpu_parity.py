@@ -224,3 +224,14 @@ def test_edge_cases(pa, oracle):
     # very low temperature: every uphill move rejected without drawing planes
     pop, _ = run_parity(pa, oracle, 3, 4, PM1, J, None, 100, np.array([0.0, 50.0, 200.0]), 2, 13)
     pop.close()
+
+
+@pytest.mark.parametrize("D,L,R,layout", [(3, 8, 640, 0), (3, 4, 1000, 2), (2, 16, 300, 0), (3, 6, 130, 0)])
+def test_low_temperature_parity(pa, oracle, D, L, R, layout):
+    """Temperatures where only dE = 4 can be accepted (beta > 8 ln 2 / 4 =
+    2.77; the uniform-threshold plane loop), on annealed populations whose
+    words are dense in dE = 4 lanes; padding lanes (R mod 64 != 0)."""
+    J = W.couplings_pm(D, L, 700 + L + D)
+    betas = np.concatenate([[0.0], np.linspace(2.8, 5.0, 11)])
+    pop, _ = run_parity(pa, oracle, D, L, PM1, J, None, R, betas, 10, 2700 + L, layout=layout)
+    pop.close()
