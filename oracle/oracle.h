@@ -69,9 +69,22 @@ or_sim* or_create_dps(int D, int L, int kind, const float* J, const float* h, in
                       const double* betas, int n_temps, int n_sweeps, uint64_t seed,
                       uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad,
                       const int32_t* populations);
+/* resampling schemes: multinomial (population exactly R_k) or nearest-integer
+ * (population R_k in expectation, Sec. II.B).  For the nearest-integer scheme
+ * R (or populations[k]) is the target and `capacity` (0: or_default_capacity
+ * of the largest target) bounds the population; copies beyond it are dropped.
+ * or_step returns -2 once the population has died out (no copies at all). */
+#define OR_RESAMPLE_MULTINOMIAL 0
+#define OR_RESAMPLE_NEAREST 1
+int     or_default_capacity(int R_max);
+or_sim* or_create_ex(int D, int L, int kind, const float* J, const float* h, int R,
+                     const double* betas, int n_temps, int n_sweeps, uint64_t seed,
+                     uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad,
+                     const int32_t* populations, int scheme, int capacity);
 int     or_current_R(const or_sim* s);
 void    or_destroy(or_sim* s);
-/* runs temperature index k = next step; returns k, or -1 after the last one */
+/* runs temperature index k = next step; returns k, -1 after the last one, -2
+ * if the population died out */
 int     or_step(or_sim* s);
 int     or_next_step(const or_sim* s);
 int     or_N(const or_sim* s);
@@ -85,6 +98,13 @@ void or_get_weights(const or_sim* s, double* w, double* P);/* R, R (last resampl
 /* out[0..7] = E_mean, E2_mean, C, lnQ, betaF, S_f, rho_s, R */
 void or_get_obs(const or_sim* s, int k, double* out);
 void or_get_grad_counts(const or_sim* s, int64_t* cJ, int64_t* ch); /* n_temps*D*N, n_temps*N */
+
+/* nearest-integer resampling of R replicas with energies E (int128 lo/hi
+ * pairs) towards `target` copies in expectation; parent has room for cap
+ * slots; returns the new population min(sum counts, cap) */
+int or_resample_nearest(int kind, int R, const int64_t* E, double beta_prev, double beta_next, int k,
+                        uint64_t seed, uint32_t inst, uint32_t tag, double target, int cap,
+                        double* w, double* P, int32_t* parent, int32_t* counts, double* lnQ);
 
 /* ---- components on explicit state (used for sampled parity at full size) ---- */
 /* spins of replicas [64*g0, 64*g0+64*ng) intersect [0,R): N_S sweeps at step k.

@@ -70,6 +70,11 @@ def lib():
                 "or_lattice": (i32, [i32, i32, vp, vp]),
                 "or_create": (vp, [i32, i32, i32, vp, vp, i32, vp, i32, i32, u64, u32, u32, i32]),
                 "or_create_dps": (vp, [i32, i32, i32, vp, vp, i32, vp, i32, i32, u64, u32, u32, i32, vp]),
+                "or_create_ex": (vp, [i32, i32, i32, vp, vp, i32, vp, i32, i32, u64, u32, u32, i32, vp,
+                                      i32, i32]),
+                "or_default_capacity": (i32, [i32]),
+                "or_resample_nearest": (i32, [i32, i32, vp, dbl, dbl, i32, u64, u32, u32, dbl, i32,
+                                              vp, vp, vp, vp, vp]),
                 "or_current_R": (i32, [vp]),
                 "or_destroy": (None, [vp]),
                 "or_step": (i32, [vp]),
@@ -196,6 +201,23 @@ def sweeps_groups(D, L, kind, J, h, beta, k, n_sweeps, seed, inst, tag, g0, ng, 
     return state
 
 
+def resample_nearest(kind, E_pairs, beta_prev, beta_next, k, seed, target, cap, inst=0, tag=0):
+    """Nearest-integer resampling of len(E_pairs)//2 replicas (Sec. II.B)."""
+    E = np.ascontiguousarray(E_pairs, dtype=np.int64)
+    R = len(E) // 2
+    w = np.empty(R); P = np.empty(R)
+    parent = np.empty(max(cap, 1), np.int32); counts = np.empty(R, np.int32)
+    lnQ = ctypes.c_double()
+    Rn = lib().or_resample_nearest(kind, R, _p(E), beta_prev, beta_next, k, seed, inst, tag,
+                                   float(target), int(cap), _p(w), _p(P), _p(parent), _p(counts),
+                                   ctypes.byref(lnQ))
+    return dict(w=w, P=P, parent=parent[:Rn], counts=counts, lnQ=lnQ.value, Rn=Rn)
+
+
+def default_capacity(R_max):
+    return lib().or_default_capacity(int(R_max))
+
+
 def overlap(N, a, b):
     a = np.ascontiguousarray(a, dtype=np.int8)
     b = np.ascontiguousarray(b, dtype=np.int8)
@@ -230,8 +252,10 @@ def exact(D, L, J, h, betas, want_corr=False):
 class Sim:
     """One oracle PAMC run (Sec. II.B), stepped one temperature at a time."""
 
+    MULTINOMIAL, NEAREST = 0, 1
+
     def __init__(self, D, L, kind, J, h, R, betas, n_sweeps, seed, rng_instance=0, rng_tag=0,
-                 accumulate_grad=False, populations=None):
+                 accumulate_grad=False, populations=None, resampling=0, capacity=0):
         self.D, self.L, self.kind, self.R = D, L, kind, R
         self.N = L ** D
         self.betas = np.ascontiguousarray(betas, dtype=np.float64)
@@ -240,9 +264,10 @@ class Sim:
         self.h = None if h is None else np.ascontiguousarray(h, dtype=np.float32)
         self.acc = bool(accumulate_grad)
         self.populations = None if populations is None else np.ascontiguousarray(populations, np.int32)
-        self._h = lib().or_create_dps(D, L, kind, _p(self.J), _p(self.h), R, _p(self.betas),
-                                      self.n_temps, n_sweeps, seed, rng_instance, rng_tag,
-                                      int(accumulate_grad), _p(self.populations))
+        self._h = lib().or_create_ex(D, L, kind, _p(self.J), _p(self.h), R, _p(self.betas),
+                                     self.n_temps, n_sweeps, seed, rng_instance, rng_tag,
+                                     int(accumulate_grad), _p(self.populations), int(resampling),
+                                     int(capacity))
         if not self._h:
             raise ValueError("oracle rejected the configuration")
 
@@ -253,6 +278,8 @@ class Sim:
             self._h = None
 
     def step(self):
+        """Runs the next temperature: its index, -1 after the last, -2 once
+        the population has died out (nearest-integer resampling)."""
         return lib().or_step(self._h)
 
     def run(self):

@@ -47,6 +47,7 @@ typedef __int128 i128;
 struct or_sim {
     int D, L, N, kind, R, G, n_temps, n_sweeps, k_next, acc_grad;
     int Rcap, R_src_last;      /* capacity; source population of the last resampling */
+    int scheme, dead;          /* resampling scheme; population died out */
     int32_t* Rk;               /* population at each temperature (Sec. III.D, Eq. 6) */
     uint64_t seed;
     uint32_t inst, tag;
@@ -320,6 +321,54 @@ static int resample_core2(int kind, int R, int Rn, const i128* E, double beta_pr
     return j == Rn ? 0 : -1;
 }
 
+/* Nearest-integer resampling R sources -> population conserved in expectation
+ * (Sec. II.B: the mean number of copies of replica i is proportional to
+ * exp[-(beta'-beta) E_i], normalised so that the expected new population is
+ * the target T = R(beta')).  tau_i = T w_i / S; replica i gets floor(tau_i)
+ * copies plus one more with probability tau_i - floor(tau_i) (uniform u_i of
+ * the RESAMPLE stream, counter (i, k, 1)).  Copies are placed as in the
+ * multinomial scheme; slots beyond the capacity are dropped.  Returns the new
+ * population min(sum n_i, cap). */
+static int resample_nearest(int kind, int R, double target, int cap, const i128* E, double beta_prev,
+                            double beta_next, int k, uint64_t seed, uint32_t inst, uint32_t tag,
+                            double* w, double* P, int32_t* parent, int32_t* counts, double* lnQ)
+{
+    double db = beta_next - beta_prev;
+    i128 emin = E[0];
+    for (int r = 1; r < R; ++r)
+        if (E[r] < emin) emin = E[r];
+    for (int r = 0; r < R; ++r) w[r] = or_spec_exp64(-(db * e_to_double(kind, E[r] - emin)));
+    double T = 0.0;
+    for (int c0 = 0; c0 < R; c0 += OR_CHUNK) {
+        double Lsum = 0.0;
+        int c1 = c0 + OR_CHUNK < R ? c0 + OR_CHUNK : R;
+        for (int i = c0; i < c1; ++i) {
+            Lsum = (i == c0) ? w[i] : Lsum + w[i];
+            P[i] = T + Lsum;
+        }
+        T = T + Lsum;
+    }
+    double S = P[R - 1];
+    *lnQ = (-(db * e_to_double(kind, emin)) + log(S)) - log((double)R);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t c3 = or_counter3(OR_STREAM_RESAMPLE, tag, inst);
+    for (int i = 0; i < R; ++i) {
+        uint32_t ctr[4] = {(uint32_t)i, (uint32_t)k, 1u, c3}, out[4];
+        or_philox4x32_10(ctr, key, out);
+        double u = or_uniform53(out[0], out[1]);
+        double tau = (target * w[i]) / S;
+        double fl = floor(tau);
+        counts[i] = (int32_t)fl + (u < tau - fl ? 1 : 0);
+    }
+    int j = 0;
+    for (int i = 0; i < R; ++i)
+        for (int t = 0; t < counts[i]; ++t) {
+            if (j < cap) parent[j] = i;
+            ++j;
+        }
+    return j < cap ? j : cap;
+}
+
 static int resample_core(int kind, int R, const i128* E, double beta_prev, double beta_next, int k,
                          uint64_t seed, uint32_t inst, uint32_t tag, double* w, double* P,
                          int32_t* parent, int32_t* counts, double* lnQ, double* u_out)
@@ -340,6 +389,20 @@ int or_resample(int kind, int R, const int64_t* E, double beta_prev, double beta
                            counts, lnQ, u_out);
     free(e);
     return rc;
+}
+
+int or_resample_nearest(int kind, int R, const int64_t* E, double beta_prev, double beta_next, int k,
+                        uint64_t seed, uint32_t inst, uint32_t tag, double target, int cap,
+                        double* w, double* P, int32_t* parent, int32_t* counts, double* lnQ)
+{
+    i128* e = (i128*)malloc(sizeof(i128) * (size_t)R);
+    if (!e) return -1;
+    for (int r = 0; r < R; ++r)
+        e[r] = (i128)(((unsigned __int128)(uint64_t)E[2 * r + 1] << 64) | (uint64_t)E[2 * r]);
+    int Rn = resample_nearest(kind, R, target, cap, e, beta_prev, beta_next, k, seed, inst, tag, w, P,
+                              parent, counts, lnQ);
+    free(e);
+    return Rn;
 }
 
 /* ---------------- the run ---------------- */
@@ -367,10 +430,37 @@ or_sim* or_create_dps(int D, int L, int kind, const float* J, const float* h, in
                       uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad,
                       const int32_t* populations)
 {
-    if (populations)
-        for (int k = 0; k < n_temps; ++k)
-            if (populations[k] < 1 || populations[k] > R) return NULL;
-    if (D < 2 || D > 3 || L < 2 || (L & 1) || R < 1 || n_temps < 1 || n_sweeps < 0) return NULL;
+    return or_create_ex(D, L, kind, J, h, R, betas, n_temps, n_sweeps, seed, rng_instance, rng_tag,
+                        accumulate_grad, populations, OR_RESAMPLE_MULTINOMIAL, 0);
+}
+
+int or_default_capacity(int R_max) { return R_max + 64 + 8 * (int)ceil(sqrt((double)R_max)); }
+
+or_sim* or_create_ex(int D, int L, int kind, const float* J, const float* h, int R,
+                     const double* betas, int n_temps, int n_sweeps, uint64_t seed,
+                     uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad,
+                     const int32_t* populations, int scheme, int capacity)
+{
+    if (R < 1 || n_temps < 1 || capacity < 0) return NULL;
+    if (scheme != OR_RESAMPLE_MULTINOMIAL && scheme != OR_RESAMPLE_NEAREST) return NULL;
+    int tmax = R;
+    if (populations) {
+        tmax = 0;
+        for (int k = 0; k < n_temps; ++k) {
+            if (populations[k] < 1) return NULL;
+            if (populations[k] > tmax) tmax = populations[k];
+        }
+    }
+    int cap;
+    if (scheme == OR_RESAMPLE_MULTINOMIAL) {
+        /* exact populations: R (or the given capacity) bounds them */
+        cap = capacity > R ? capacity : R;
+        if (tmax > cap) return NULL;
+    } else {
+        cap = capacity > 0 ? capacity : or_default_capacity(tmax);
+        if (tmax > cap) return NULL;
+    }
+    if (D < 2 || D > 3 || L < 2 || (L & 1) || n_temps < 1 || n_sweeps < 0) return NULL;
     if (kind != OR_PM1 && kind != OR_REAL) return NULL;
     if (betas[0] != 0.0) return NULL;
     for (int k = 1; k < n_temps; ++k)
@@ -378,7 +468,7 @@ or_sim* or_create_dps(int D, int L, int kind, const float* J, const float* h, in
     or_sim* s = (or_sim*)calloc(1, sizeof(or_sim));
     int N = ipow(L, D);
     s->D = D; s->L = L; s->N = N; s->kind = kind; s->R = R; s->G = (R + 63) / 64;
-    s->Rcap = R; s->R_src_last = R;
+    s->Rcap = cap; s->R_src_last = R; s->scheme = scheme; s->dead = 0;
     s->Rk = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_temps);
     for (int k = 0; k < n_temps; ++k) s->Rk[k] = populations ? populations[k] : R;
     s->n_temps = n_temps; s->n_sweeps = n_sweeps; s->k_next = 0; s->acc_grad = accumulate_grad;
@@ -405,15 +495,15 @@ or_sim* or_create_dps(int D, int L, int kind, const float* J, const float* h, in
     s->nbr = (int32_t*)malloc(sizeof(int32_t) * (size_t)N * 2 * D);
     s->bond = (int32_t*)malloc(sizeof(int32_t) * (size_t)N * 2 * D);
     or_lattice(D, L, s->nbr, s->bond);
-    s->s = (int8_t*)malloc((size_t)R * N);
-    s->tmp = (int8_t*)malloc((size_t)R * N);
-    s->E = (i128*)calloc((size_t)R, sizeof(i128));
-    s->parent = (int32_t*)malloc(sizeof(int32_t) * (size_t)R);
-    s->family = (int32_t*)malloc(sizeof(int32_t) * (size_t)R);
-    s->family_tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)R);
-    s->counts = (int32_t*)malloc(sizeof(int32_t) * (size_t)R);
-    s->w = (double*)calloc((size_t)R, sizeof(double));
-    s->P = (double*)calloc((size_t)R, sizeof(double));
+    s->s = (int8_t*)malloc((size_t)cap * N);
+    s->tmp = (int8_t*)malloc((size_t)cap * N);
+    s->E = (i128*)calloc((size_t)cap, sizeof(i128));
+    s->parent = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+    s->family = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+    s->family_tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+    s->counts = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+    s->w = (double*)calloc((size_t)cap, sizeof(double));
+    s->P = (double*)calloc((size_t)cap, sizeof(double));
     s->obs = (double*)calloc((size_t)n_temps * 8, sizeof(double));
     if (accumulate_grad) {
         s->cJ = (int64_t*)calloc((size_t)n_temps * D * N, sizeof(int64_t));
@@ -497,6 +587,7 @@ static void measure(or_sim* s, int k, double lnQ)
 int or_step(or_sim* s)
 {
     int k = s->k_next;
+    if (s->dead) return -2;
     if (k >= s->n_temps) return -1;
     double lnQ = 0.0;
     if (k == 0) {
@@ -504,9 +595,22 @@ int or_step(or_sim* s)
         init_spins(s->N, s->R, s->seed, s->inst, s->tag, s->s);
         for (int r = 0; r < s->R; ++r) s->family[r] = s->parent[r] = r;
     } else {
-        const int Rn = s->Rk[k];
-        resample_core2(s->kind, s->R, Rn, s->E, s->betas[k - 1], s->betas[k], k, s->seed, s->inst,
-                       s->tag, s->w, s->P, s->parent, s->counts, &lnQ, NULL);
+        int Rn = s->Rk[k];
+        if (s->scheme == OR_RESAMPLE_NEAREST) {
+            Rn = resample_nearest(s->kind, s->R, (double)s->Rk[k], s->Rcap, s->E, s->betas[k - 1],
+                                  s->betas[k], k, s->seed, s->inst, s->tag, s->w, s->P, s->parent,
+                                  s->counts, &lnQ);
+            if (Rn == 0) { /* every replica left without copies: the run ends */
+                s->dead = 1;
+                s->R_src_last = s->R;
+                s->R = 0;
+                s->k_next = k + 1;
+                return -2;
+            }
+        } else {
+            resample_core2(s->kind, s->R, Rn, s->E, s->betas[k - 1], s->betas[k], k, s->seed, s->inst,
+                           s->tag, s->w, s->P, s->parent, s->counts, &lnQ, NULL);
+        }
         s->R_src_last = s->R;
         s->R = Rn;
         for (int j = 0; j < s->R; ++j) {

@@ -471,3 +471,110 @@ def test_dynamic_population_matches_exact(oracle, case):
         assert _z([r["bF"][k] for r in recs], ex["betaF"][k]) < 5
         ratio = math.exp(ex["lnZ"][k] - ex["lnZ"][0])
         assert _z([math.exp(r["lnQsum"][k]) / ratio for r in recs], 1.0) < 5
+
+
+# ---------------- nearest-integer resampling (Sec. II.B: population in expectation) ----------------
+
+def _pairs_pm(E):
+    E = np.asarray(E, np.int64)
+    return np.stack([E, np.where(E < 0, -1, 0)], 1).reshape(-1)
+
+
+def test_nearest_copy_numbers_law(oracle):
+    """n_i is floor(tau_i) or ceil(tau_i) with mean tau_i = T w_i / sum w
+    (weights recomputed with numpy's exp), and the population sum n_i has
+    mean T and variance sum frac(tau)(1 - frac(tau))."""
+    rng = np.random.default_rng(5)
+    R, T = 300, 280.0
+    E = rng.integers(-40, 40, R) * 4
+    b0, b1 = 0.2, 0.23
+    w = np.exp(-(b1 - b0) * (E - E.min()))
+    tau = T * w / w.sum()
+    M = 400
+    n = np.zeros((M, R))
+    tot = np.zeros(M)
+    for m in range(M):
+        res = oracle.resample_nearest(PM1, _pairs_pm(E), b0, b1, 1 + m, 77, T, 10 ** 6)
+        n[m] = res["counts"]
+        tot[m] = res["Rn"]
+        assert res["Rn"] == n[m].sum()
+        np.testing.assert_array_equal(np.bincount(res["parent"], minlength=R), res["counts"])
+        assert np.all(np.diff(res["parent"]) >= 0)
+    assert np.all((n == np.floor(tau)) | (n == np.ceil(tau)))
+    fr = tau - np.floor(tau)
+    z = (n.mean(0) - tau) / np.sqrt(np.maximum(fr * (1 - fr), 1e-12) / M)
+    assert np.abs(z[fr > 1e-3]).max() < 5
+    chi2 = (z[fr > 1e-3] ** 2).sum()
+    dof = int((fr > 1e-3).sum())
+    assert abs(chi2 - dof) < 6 * math.sqrt(2 * dof)
+    var = (fr * (1 - fr)).sum()
+    assert abs(tot.mean() - T) < 5 * math.sqrt(var / M)
+    assert tot.var(ddof=1) == pytest.approx(var, rel=0.25)
+
+
+def test_nearest_integer_targets_are_exact(oracle):
+    """Equal weights and T a multiple of R: tau_i = T / R is an integer, so
+    every replica gets exactly T / R copies and the population is exactly T."""
+    E = np.full(300, -12)
+    for T, beta1 in ((600.0, 0.0), (300.0, 0.7), (900.0, 2.0)):
+        res = oracle.resample_nearest(PM1, _pairs_pm(E), 0.0, beta1, 2, 5, T, 10 ** 6)
+        assert res["Rn"] == int(T)
+        assert np.all(res["counts"] == int(T) // 300)
+        assert res["lnQ"] == pytest.approx(12 * beta1, rel=1e-15, abs=1e-15)
+
+
+def test_nearest_capacity_truncates_the_placement(oracle):
+    rng = np.random.default_rng(6)
+    E = rng.integers(-10, 10, 200) * 4
+    full = oracle.resample_nearest(PM1, _pairs_pm(E), 0.0, 0.5, 3, 91, 200.0, 10 ** 6)
+    for cap in (1, 50, full["Rn"] - 1, full["Rn"], full["Rn"] + 10):
+        cut = oracle.resample_nearest(PM1, _pairs_pm(E), 0.0, 0.5, 3, 91, 200.0, cap)
+        assert cut["Rn"] == min(cap, full["Rn"])
+        np.testing.assert_array_equal(cut["parent"], full["parent"][:cut["Rn"]])
+        np.testing.assert_array_equal(cut["counts"], full["counts"])
+        assert cut["lnQ"] == full["lnQ"]
+
+
+def test_nearest_population_dies_out(oracle):
+    """Two replicas at equal energy and a target of one copy: tau = 1/2 each,
+    so the population is empty with probability 1/4; or_step reports it."""
+    D, L = 3, 2
+    J = W.couplings_pm(D, L, 1)
+    betas = [0.0, 0.0, 0.0]
+    died = 0
+    for sd in range(64):
+        s = oracle.Sim(D, L, PM1, J, None, 2, betas, 0, sd, populations=[2, 1, 1], resampling=1)
+        assert s.step() == 0
+        r = s.step()
+        if r == -2:
+            died += 1
+            assert s.R_now == 0 and s.step() == -2
+        else:
+            assert r == 1 and s.R_now in (1, 2)
+    assert 4 <= died <= 32  # binomial(64, 1/4): mean 16
+
+
+@pytest.mark.parametrize("case", ["pm_3d_L2", "real_2d_L4_field"])
+def test_nearest_anneal_matches_exact(oracle, case):
+    if case == "pm_3d_L2":
+        D, L, kind = 3, 2, PM1
+        J, h = W.couplings_pm(D, L, 321), None
+        betas = W.schedule_lb(11, 2.0)
+    else:
+        D, L, kind = 2, 4, REAL
+        J, h = W.couplings_pm(D, L, 322), W.field_uniform(16, 323)
+        betas = W.schedule_lb(11, 1.5)
+    ex = oracle.exact(D, L, J.astype(np.float64), None if h is None else h.astype(np.float64), betas)
+    recs, Rs = [], []
+    for sd in range(4000, 4016):
+        s = oracle.Sim(D, L, kind, J, h, 1500, betas, 6, sd, resampling=1)
+        s.run()
+        o = [s.obs(k) for k in range(len(betas))]
+        recs.append(dict(E=np.array([x["E_mean"] for x in o]), bF=np.array([x["betaF"] for x in o])))
+        Rs.append([x["R"] for x in o])
+    for k in (3, 6, 10):
+        assert _z([r["E"][k] for r in recs], ex["E"][k]) < 5
+        assert _z([r["bF"][k] for r in recs], ex["betaF"][k]) < 5
+    Rs = np.array(Rs)
+    assert Rs[:, 0].min() == 1500 and abs(Rs[:, 1:].mean() - 1500) < 20
+    assert Rs[:, 1:].std() > 0  # the population fluctuates
