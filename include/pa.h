@@ -45,11 +45,19 @@ enum {
     PA_ECUDA = -3,    /* a CUDA call failed (message has the CUDA error)        */
     PA_ETIMEOUT = -4, /* a bounded device wait gave up                           */
     PA_EDONE = -5,    /* the schedule is finished                                */
-    PA_ESTATE = -6    /* call not valid in the current state                     */
+    PA_ESTATE = -6,   /* call not valid in the current state                     */
+    PA_EEMPTY = -7    /* the population died out (nearest-integer resampling)    */
 };
 
 enum { PA_PM1 = 0, /* J in {-1,+1}, no field */
        PA_REAL = 1 /* FP32 couplings, optional FP32 field */ };
+
+/* Resampling (Sec. II.B: replica i gets on average R(beta') w_i / sum_j w_j
+ * copies, w_i = exp[-(beta'-beta) E_i]). */
+enum { PA_RESAMPLE_MULTINOMIAL = 0, /* R(beta') independent draws: population exactly R(beta') */
+       PA_RESAMPLE_NEAREST = 1 };   /* floor(tau_i) copies, one more with probability
+                                     * tau_i - floor(tau_i), tau_i = R(beta') w_i / sum w:
+                                     * population R(beta') in expectation */
 
 enum { PA_LAYOUT_AUTO = 0,   /* PM1 -> packed, REAL -> int8                          */
        PA_LAYOUT_PACKED = 1, /* PM1 only: 64 replicas per uint64 word, bit 1 = spin -1 */
@@ -63,9 +71,17 @@ typedef struct {
     int32_t threads;         /* 0 = tuned default; else threads per block              */
     int32_t groups_per_block;/* 0 = tuned default (packed layout)                      */
     /* dynamic population (Sec. III.D, Eq. 6): host array of n_temps replica
-     * counts, 1 <= populations[k] <= R (R is then the capacity); resampling into
-     * temperature k draws populations[k] copies.  NULL keeps R throughout. */
+     * counts, populations[k] >= 1, the population R(beta_k) at temperature k
+     * (exact for the multinomial scheme, the expectation for the
+     * nearest-integer one).  NULL keeps R throughout. */
     const int32_t* populations;
+    int32_t resampling;      /* PA_RESAMPLE_*                                          */
+    /* replica slots (buffers, grids).  Multinomial: max(R, capacity), and every
+     * populations[k] must fit.  Nearest-integer: 0 selects T + 64 + 8 ceil(sqrt T)
+     * for the largest target T; copies placed beyond the capacity are dropped.
+     * Kernels then read the population from device memory, so one CUDA graph
+     * serves any population sequence. */
+    int32_t capacity;
 } pa_options;
 
 /* Per-temperature observables (Sec. II.B, Eq. 2-3; Sec. V.A, Eq. 9). */
@@ -149,9 +165,11 @@ int pa_grad(pa_ctx* ctx, const double* gbar, double* dJ, double* dh);
  * (N + sum_i S^a_i S^b_i) / 2. */
 int pa_overlap(pa_ctx* a, pa_ctx* b, int64_t* hist);
 
-/* Copies of the current state to host memory (synchronise).  With a dynamic
- * population the current population is populations[last completed step]
- * (pa_sizes reports it as R). */
+/* Copies of the current state to host memory (synchronise).  R below is the
+ * current population: populations[last completed step] for the multinomial
+ * scheme, the drawn population for the nearest-integer one (pa_sizes reports
+ * it).  PA_EEMPTY once a nearest-integer resampling left no replica (every
+ * later step does no work). */
 int pa_get_spins(pa_ctx* ctx, int8_t* host_spins /* R*N, +1/-1, replica-major */);
 /* Replicas [r0, r0 + n) only (0 <= r0, r0 + n <= R): n*N bytes, +1/-1. */
 int pa_get_spins_range(pa_ctx* ctx, int r0, int n, int8_t* host_spins);

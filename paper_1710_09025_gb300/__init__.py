@@ -21,7 +21,8 @@ from . import workloads  # noqa: F401  (seeded synthetic inputs)
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libpamc.so")
 
-PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ETIMEOUT, PA_EDONE, PA_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ETIMEOUT, PA_EDONE, PA_ESTATE, PA_EEMPTY = 0, -1, -2, -3, -4, -5, -6, -7
+PA_RESAMPLE_MULTINOMIAL, PA_RESAMPLE_NEAREST = 0, 1
 PA_PM1, PA_REAL = 0, 1
 PA_LAYOUT_AUTO, PA_LAYOUT_PACKED, PA_LAYOUT_I8 = 0, 1, 2
 
@@ -39,7 +40,8 @@ class pa_options(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int32), ("accumulate_grad", ctypes.c_int32),
                 ("rng_instance", ctypes.c_uint32), ("rng_tag", ctypes.c_uint32),
                 ("threads", ctypes.c_int32), ("groups_per_block", ctypes.c_int32),
-                ("populations", ctypes.c_void_p)]
+                ("populations", ctypes.c_void_p), ("resampling", ctypes.c_int32),
+                ("capacity", ctypes.c_int32)]
 
 
 class pa_inst_desc(ctypes.Structure):

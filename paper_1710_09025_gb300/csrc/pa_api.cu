@@ -29,7 +29,9 @@ struct pa_ctx {
     int gpb, threads, real_warps;
     double betaF0, log_R;
     std::vector<double> betas;
-    std::vector<int> Rk;        // population at each temperature (R = capacity)
+    std::vector<int> Rk;        // population (target) at each temperature; R = capacity
+    int scheme;                 // PA_RESAMPLE_*; nearest-integer: populations in Rdev
+    int* Rdev;                  // [n_temps] populations in device memory
     std::vector<float> Jh, hh;  // flushed host copies
     // device
     void* ws;
@@ -113,8 +115,9 @@ __global__ void iota_kernel(int32_t* a, int32_t* b, int n)
     }
 }
 
-__global__ void acc0_kernel(StepAcc* acc, double betaF0, int R)
+__global__ void acc0_kernel(StepAcc* acc, double betaF0, int R, int* Rdev)
 {
+    *Rdev = R;
     acc->lnQ = 0.0;
     acc->sum_lnQ = 0.0;
     acc->betaF = betaF0;
@@ -131,7 +134,7 @@ struct Layout {
 enum {
     W_J, W_H, W_JNEG, W_JFIX, W_HFIX, W_BETAS, W_S0, W_S1, W_E32, W_E128, W_PARENT, W_FAM0, W_FAM1,
     W_COUNTS, W_BLOCKSUM, W_W, W_P, W_TOT, W_T, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
-    W_DH, W_OBSPART, W_RK, W_COUNT
+    W_DH, W_OBSPART, W_RK, W_RDEV, W_COUNT
 };
 
 static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps, int acc_grad)
@@ -171,6 +174,7 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
     sz[W_DH] = acc_grad ? sizeof(double) * N : 0;
     sz[W_OBSPART] = sizeof(pa::ObsPartial) * pa::kObsBlocks;
     sz[W_RK] = sizeof(double) * n_temps;
+    sz[W_RDEV] = sizeof(int) * n_temps;
     Layout lay;
     size_t off = 0;
     for (int i = 0; i < W_COUNT; ++i) {
@@ -182,6 +186,23 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
 }
 
 // ---------------- validation ----------------
+
+// replica slots: the multinomial scheme draws exact populations (at most
+// max(R, capacity)); the nearest-integer scheme fluctuates around its targets
+// (the largest target T, default capacity T + 64 + 8 ceil(sqrt T))
+static long long capacity_of(int R, int n_temps, const pa_options* o)
+{
+    const int scheme = o ? o->resampling : PA_RESAMPLE_MULTINOMIAL;
+    const int given = o ? o->capacity : 0;
+    if (scheme == PA_RESAMPLE_MULTINOMIAL) return given > R ? given : R;
+    long long tmax = R;
+    if (o && o->populations) {
+        tmax = 0;
+        for (int k = 0; k < n_temps; ++k) tmax = std::max<long long>(tmax, o->populations[k]);
+    }
+    if (given > 0) return given;
+    return tmax + 64 + 8 * (long long)std::ceil(std::sqrt((double)tmax));
+}
 
 static int resolve_layout(int kind, const pa_options* o)
 {
@@ -227,10 +248,21 @@ static int validate(std::string& err, int D, int L, int kind, const float* J, co
         if (o->accumulate_grad && kind != PA_REAL) { err = "accumulate_grad needs PA_REAL"; return PA_EINVAL; }
         if (o->rng_instance >= (1u << 24)) { err = "rng_instance must be < 2^24"; return PA_EINVAL; }
         if (o->rng_tag >= 16u) { err = "rng_tag must be < 16"; return PA_EINVAL; }
+        if (o->resampling != PA_RESAMPLE_MULTINOMIAL && o->resampling != PA_RESAMPLE_NEAREST) {
+            err = "resampling must be PA_RESAMPLE_MULTINOMIAL or PA_RESAMPLE_NEAREST";
+            return PA_EINVAL;
+        }
+        if (o->capacity < 0) { err = "capacity must be >= 0"; return PA_EINVAL; }
+        const long long cap = capacity_of(R, n_temps, o);
+        if (cap > (1 << 26)) { err = "capacity must be <= 2^26"; return PA_EINVAL; }
+        if (o->resampling == PA_RESAMPLE_NEAREST && !o->populations && cap < R) {
+            err = "capacity below the population R";
+            return PA_EINVAL;
+        }
         if (o->populations)
             for (int k = 0; k < n_temps; ++k)
-                if (o->populations[k] < 1 || o->populations[k] > R) {
-                    err = "populations[k] must be in [1, R]";
+                if (o->populations[k] < 1 || o->populations[k] > cap) {
+                    err = "populations[k] must be in [1, capacity]";
                     return PA_EINVAL;
                 }
     }
@@ -251,7 +283,9 @@ extern "C" int pa_workspace_size(int D, int L, int kind, int R, int n_temps, con
 {
     if (!bytes || (D != 2 && D != 3) || L < 2 || R < 1 || n_temps < 1) return PA_EINVAL;
     int lay = resolve_layout(kind, opt);
-    Layout l = make_layout(D, L, kind, lay, R, n_temps, opt ? opt->accumulate_grad : 0);
+    const long long cap = capacity_of(R, n_temps, opt);
+    if (cap > (1 << 26)) return PA_EINVAL;
+    Layout l = make_layout(D, L, kind, lay, (int)cap, n_temps, opt ? opt->accumulate_grad : 0);
     *bytes = l.total;
     return PA_OK;
 }
@@ -279,8 +313,9 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     pa_options_default(&o);
     if (opt) o = *opt;
     pa_ctx* c = new pa_ctx();
-    c->D = D; c->L = L; c->N = (D == 3) ? L * L * L : L * L; c->kind = kind; c->R = R;
-    c->G = (R + 63) / 64; c->n_temps = n_temps; c->n_sweeps = n_sweeps; c->k_next = 0;
+    const int cap = (int)capacity_of(R, n_temps, &o);
+    c->D = D; c->L = L; c->N = (D == 3) ? L * L * L : L * L; c->kind = kind; c->R = cap;
+    c->G = (cap + 63) / 64; c->scheme = o.resampling; c->n_temps = n_temps; c->n_sweeps = n_sweeps; c->k_next = 0;
     c->layout = resolve_layout(kind, &o); c->NP = (c->N + 15) / 16 * 16;
     c->seed = seed; c->inst = o.rng_instance; c->tag = o.rng_tag; c->acc_grad = o.accumulate_grad ? 1 : 0;
     c->st = (cudaStream_t)stream;
@@ -312,7 +347,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
         }
     if (nflush) c->err = "warning: " + std::to_string(nflush) + " coupling/field magnitudes below 2^-73 flushed to 0";
 
-    Layout lay = make_layout(D, L, kind, c->layout, R, n_temps, c->acc_grad);
+    Layout lay = make_layout(D, L, kind, c->layout, cap, n_temps, c->acc_grad);
     if (workspace) {
         if (ws_bytes < lay.total || ((uintptr_t)workspace & 255)) {
             g_create_err = "workspace too small or not 256-byte aligned";
@@ -358,6 +393,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->dh_d = c->acc_grad ? (double*)at(W_DH) : nullptr;
     c->obspart = (pa::ObsPartial*)at(W_OBSPART);
     c->Rk_d = (double*)at(W_RK);
+    c->Rdev = (int*)at(W_RDEV);
 
     // couplings: sign masks (+-J), fixed-point copies (real)
     std::vector<uint8_t> jn(N, 0);
@@ -488,10 +524,18 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
     const double beta = c->betas[k];
     std::memset(pl, 0, sizeof *pl);
     pl->k = k;
+    // nearest-integer scheme: every kernel reads the population from Rdev and
+    // the grids cover the capacity
+    const bool dyn = c->scheme == PA_RESAMPLE_NEAREST;
     if (k > 0) {
         pa::ResampleArgs& ra = pl->rs;
         const int Rprev = c->Rk[k - 1];
         ra.R = Rprev; ra.Rn = R; ra.kind = c->kind == PA_PM1 ? 0 : 1;
+        if (dyn) {
+            ra.R = c->R; ra.Rn = 0;
+            ra.scheme = 1; ra.cap = c->R; ra.target = (double)c->Rk[k];
+            ra.Rsrc = c->Rdev + (k - 1); ra.Rdst = c->Rdev + k; ra.Rdst_d = c->Rk_d + k;
+        }
         ra.E32 = c->E32; ra.E128 = c->E128;
         ra.prev = c->acc + (k - 1); ra.cur = c->acc + k;
         ra.w = c->w; ra.P = c->P; ra.tot = c->tot; ra.T = c->T;
@@ -506,6 +550,7 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         fill_packed_step(&pl->pk.s, c->D, beta, k, c->n_sweeps, k0, k1);
         pa::PackedInst& in = pl->pk.i;
         in.jneg = c->jneg; in.E = c->E32; in.G = G; in.R = R; in.NP = c->NP;
+        if (dyn) { in.Rdev = c->Rdev + k; in.G = c->G; in.R = c->R; }
         in.c3 = pa::counter3(pa::STREAM_PLANE, c->tag, c->inst);
         if (c->layout == PA_LAYOUT_PACKED) {
             // k > 0: the replica gather is fused into the sweep's tile load
@@ -530,10 +575,12 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         in.cJ = c->acc_grad ? c->cJ + (size_t)k * c->D * c->N : nullptr;
         in.ch = c->acc_grad ? c->ch + (size_t)k * c->N : nullptr;
         in.R = R; in.NP = c->NP; in.c3 = pa::counter3(pa::STREAM_WORD, c->tag, c->inst);
+        if (dyn) { in.Rdev = c->Rdev + k; in.R = c->R; }
         c->cur ^= 1;
     }
     pa::ObsArgs& oa = pl->ob;
     oa.R = R; oa.kind = c->kind == PA_PM1 ? 0 : 1; oa.E32 = c->E32; oa.E128 = c->E128;
+    if (dyn) { oa.Rdev = c->Rdev + k; oa.R = c->R; }
     oa.family = c->fam[c->famcur]; oa.part = c->obspart; oa.cur = c->acc + k;
     c->k_next = k + 1;
     pl->cur = c->cur;
@@ -551,7 +598,7 @@ static int enqueue_init(pa_ctx* c)
     else
         PA_CK(c, pa::launch_init_i8(c->S8[c->cur], c->N, c->NP, R0, k0, k1, c3, c->st));
     iota_kernel<<<(c->R + 255) / 256, 256, 0, c->st>>>(c->fam[c->famcur], c->parent, c->R);
-    acc0_kernel<<<1, 1, 0, c->st>>>(c->acc, c->betaF0, R0);
+    acc0_kernel<<<1, 1, 0, c->st>>>(c->acc, c->betaF0, R0, c->Rdev);
     PA_CK(c, cudaGetLastError());
     c->launches += 3;
     return PA_OK;
@@ -647,11 +694,32 @@ extern "C" int pa_anneal(pa_ctx* c, int n_steps)
 
 extern "C" int pa_current_step(const pa_ctx* c) { return c ? c->k_next : PA_EINVAL; }
 
+// population after the last completed step (before any step: the initial
+// one); the nearest-integer scheme keeps it in device memory (synchronises)
+static int pop_now(pa_ctx* c, int* R)
+{
+    const int k = c->k_next > 0 ? c->k_next - 1 : 0;
+    *R = c->Rk[k];
+    if (c->scheme == PA_RESAMPLE_NEAREST && c->k_next > 0) {
+        PA_CK(c, cudaMemcpyAsync(R, c->Rdev + k, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        PA_CK(c, cudaStreamSynchronize(c->st));
+        if (*R == 0) { c->err = "population died out"; return PA_EEMPTY; }
+    }
+    return PA_OK;
+}
+#define PA_POP(ctx, var)                      \
+    int var;                                  \
+    do {                                      \
+        int rc__ = pop_now((ctx), &var);      \
+        if (rc__ != PA_OK) return rc__;       \
+    } while (0)
+
 extern "C" int pa_synchronize(pa_ctx* c)
 {
     if (!c) return PA_EINVAL;
     PA_CK(c, cudaStreamSynchronize(c->st));
-    return PA_OK;
+    int R;
+    return pop_now(c, &R);  // PA_EEMPTY once the population died out
 }
 
 extern "C" int pa_observables(pa_ctx* c, int k, pa_obs* out)
@@ -659,9 +727,13 @@ extern "C" int pa_observables(pa_ctx* c, int k, pa_obs* out)
     if (!c || !out) return PA_EINVAL;
     if (k < 0 || k >= c->k_next) { c->err = "step not run yet"; return PA_ESTATE; }
     StepAcc a;
+    int Rk = c->Rk[k];
     PA_CK(c, cudaMemcpyAsync(&a, c->acc + k, sizeof a, cudaMemcpyDeviceToHost, c->st));
+    if (c->scheme == PA_RESAMPLE_NEAREST)
+        PA_CK(c, cudaMemcpyAsync(&Rk, c->Rdev + k, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     PA_CK(c, cudaStreamSynchronize(c->st));
-    const double R = (double)c->Rk[k];
+    if (Rk == 0) { c->err = "population died out"; return PA_EEMPTY; }
+    const double R = (double)Rk;
     double Em, E2m;
     if (c->kind == PA_PM1) {
         Em = (double)a.sumE / R;
@@ -678,7 +750,7 @@ extern "C" int pa_observables(pa_ctx* c, int k, pa_obs* out)
     out->betaF = a.betaF;
     out->S_f = std::log(R) - a.sum_clnc / R;
     out->rho_s = R / std::exp(out->S_f);
-    out->R = c->Rk[k];
+    out->R = Rk;
     return PA_OK;
 }
 
@@ -708,22 +780,21 @@ extern "C" int pa_grad(pa_ctx* c, const double* gbar, double* dJ, double* dh)
     return PA_OK;
 }
 
-// population after the last completed step (before any step: the initial one)
-static int pop_now(const pa_ctx* c) { return c->Rk[c->k_next > 0 ? c->k_next - 1 : 0]; }
-
 extern "C" int pa_overlap(pa_ctx* a, pa_ctx* b, int64_t* hist)
 {
     if (!a || !b || !hist) return PA_EINVAL;
-    if (a->D != b->D || a->L != b->L || pop_now(a) != pop_now(b) || a->layout != b->layout) {
+    PA_POP(a, Ra);
+    PA_POP(b, Rb);
+    if (a->D != b->D || a->L != b->L || Ra != Rb || a->layout != b->layout) {
         a->err = "overlap needs two contexts of the same lattice, R and layout";
         return PA_EINVAL;
     }
     PA_CK(a, cudaStreamSynchronize(b->st));
     PA_CK(a, cudaMemsetAsync(a->hist, 0, sizeof(unsigned long long) * (a->N + 1), a->st));
     if (a->layout == PA_LAYOUT_PACKED)
-        PA_CK(a, pa::launch_overlap_packed(a->S[a->cur], b->S[b->cur], a->N, pop_now(a), a->hist, a->st));
+        PA_CK(a, pa::launch_overlap_packed(a->S[a->cur], b->S[b->cur], a->N, Ra, a->hist, a->st));
     else
-        PA_CK(a, pa::launch_overlap_i8(a->S8[a->cur], b->S8[b->cur], a->N, a->NP, pop_now(a), a->hist, a->st));
+        PA_CK(a, pa::launch_overlap_i8(a->S8[a->cur], b->S8[b->cur], a->N, a->NP, Ra, a->hist, a->st));
     PA_CK(a, cudaMemcpyAsync(hist, a->hist, sizeof(int64_t) * (a->N + 1), cudaMemcpyDeviceToHost, a->st));
     PA_CK(a, cudaStreamSynchronize(a->st));
     return PA_OK;
@@ -731,7 +802,9 @@ extern "C" int pa_overlap(pa_ctx* a, pa_ctx* b, int64_t* hist)
 
 extern "C" int pa_get_spins_range(pa_ctx* c, int r0, int n, int8_t* dst)
 {
-    if (!c || !dst || r0 < 0 || n < 0 || r0 + n > pop_now(c)) return PA_EINVAL;
+    if (!c || !dst) return PA_EINVAL;
+    PA_POP(c, Rn);
+    if (r0 < 0 || n < 0 || r0 + n > Rn) return PA_EINVAL;
     if (n == 0) return PA_OK;
     if (c->layout == PA_LAYOUT_PACKED) {
         PA_CK(c, pa::launch_unpack_packed(c->S[c->cur], c->tmp8, c->N, r0, n, c->st));
@@ -747,13 +820,14 @@ extern "C" int pa_get_spins_range(pa_ctx* c, int r0, int n, int8_t* dst)
 extern "C" int pa_get_spins(pa_ctx* c, int8_t* dst)
 {
     if (!c) return PA_EINVAL;
-    return pa_get_spins_range(c, 0, pop_now(c), dst);
+    PA_POP(c, Rn);
+    return pa_get_spins_range(c, 0, Rn, dst);
 }
 
 extern "C" int pa_get_energies(pa_ctx* c, int64_t* dst)
 {
     if (!c || !dst) return PA_EINVAL;
-    const int Rn = pop_now(c);
+    PA_POP(c, Rn);
     if (c->kind == PA_PM1) {
         std::vector<int32_t> e(Rn);
         PA_CK(c, cudaMemcpyAsync(e.data(), c->E32, sizeof(int32_t) * Rn, cudaMemcpyDeviceToHost, c->st));
@@ -769,7 +843,8 @@ extern "C" int pa_get_energies(pa_ctx* c, int64_t* dst)
 extern "C" int pa_get_parents(pa_ctx* c, int32_t* dst)
 {
     if (!c || !dst) return PA_EINVAL;
-    PA_CK(c, cudaMemcpyAsync(dst, c->parent, sizeof(int32_t) * pop_now(c), cudaMemcpyDeviceToHost, c->st));
+    PA_POP(c, Rn);
+    PA_CK(c, cudaMemcpyAsync(dst, c->parent, sizeof(int32_t) * Rn, cudaMemcpyDeviceToHost, c->st));
     PA_CK(c, cudaStreamSynchronize(c->st));
     return PA_OK;
 }
@@ -777,7 +852,8 @@ extern "C" int pa_get_parents(pa_ctx* c, int32_t* dst)
 extern "C" int pa_get_family(pa_ctx* c, int32_t* dst)
 {
     if (!c || !dst) return PA_EINVAL;
-    PA_CK(c, cudaMemcpyAsync(dst, c->fam[c->famcur], sizeof(int32_t) * pop_now(c), cudaMemcpyDeviceToHost, c->st));
+    PA_POP(c, Rn);
+    PA_CK(c, cudaMemcpyAsync(dst, c->fam[c->famcur], sizeof(int32_t) * Rn, cudaMemcpyDeviceToHost, c->st));
     PA_CK(c, cudaStreamSynchronize(c->st));
     return PA_OK;
 }
@@ -798,7 +874,10 @@ extern "C" int pa_sizes(const pa_ctx* c, int* D, int* L, int* N, int* R, int* n_
     if (D) *D = c->D;
     if (L) *L = c->L;
     if (N) *N = c->N;
-    if (R) *R = pop_now(c);
+    if (R) {
+        int rc = pop_now(const_cast<pa_ctx*>(c), R);
+        if (rc != PA_OK && rc != PA_EEMPTY) return rc;  // an empty population reports R = 0
+    }
     if (n_temps) *n_temps = c->n_temps;
     if (layout) *layout = c->layout;
     return PA_OK;
@@ -932,8 +1011,10 @@ extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_
     *out = nullptr;
     if (D != 3) { g_create_err = "batched sweeps support D = 3"; return PA_EINVAL; }
     if (n_inst < 1 || !descs) { g_create_err = "need at least one instance"; return PA_EINVAL; }
-    if (opt && (opt->layout != PA_LAYOUT_AUTO || opt->accumulate_grad || opt->populations)) {
-        g_create_err = "batch: layout must be AUTO, accumulate_grad 0 and populations NULL";
+    if (opt && (opt->layout != PA_LAYOUT_AUTO || opt->accumulate_grad || opt->populations ||
+                opt->resampling != PA_RESAMPLE_MULTINOMIAL || opt->capacity)) {
+        g_create_err = "batch: layout must be AUTO, accumulate_grad 0, populations NULL, multinomial "
+                       "resampling and no capacity";
         return PA_EINVAL;
     }
     pa_batch* b = new pa_batch();

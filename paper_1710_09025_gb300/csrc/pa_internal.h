@@ -42,6 +42,7 @@ struct PackedInst {
     int8_t* S8_in;           // int8 storage of the same algorithm (layout I8): rows of NP bytes
     int8_t* S8_out;          // non-null selects the int8 storage
     const int32_t* parent;   // or null (identity)
+    const int* Rdev;         // population in device memory (or null: R); G, R then size the grid
     int G, R, NP;
     uint32_t c3;             // Philox counter word 3 of the PLANE stream
 };
@@ -76,6 +77,7 @@ struct RealInst {
     longlong2* E;            // [R] energies * 2^96 out
     unsigned long long* cJ;  // [D*N] grad counts of this step (or null)
     unsigned long long* ch;  // [N]
+    const int* Rdev;         // population in device memory (or null: R); R then sizes the grid
     int R, NP;
     uint32_t c3;             // Philox counter word 3 of the WORD stream
 };
@@ -109,6 +111,13 @@ cudaError_t launch_sweep_batched(const PackedStep& ps, const RealStep& rs, const
 struct ResampleArgs {
     int R, kind;                 // R: source replicas; kind 0: E32, 1: E128
     int Rn;                      // copies drawn (the new population)
+    // nearest-integer scheme (scheme 1): populations live in device memory;
+    // R above is then the capacity and sizes the grids
+    int scheme, cap;
+    double target;               // expected new population R(beta')
+    const int* Rsrc;             // source population (or null: R)
+    int* Rdst;                   // new population min(sum n_i, cap) out
+    double* Rdst_d;              // the same as a double (gradient normalisation)
     const int32_t* E32;
     const longlong2* E128;
     const StepAcc* prev;         // acc[k-1]: E_min, sum_lnQ
@@ -139,6 +148,7 @@ struct ObsPartial {
 constexpr int kObsBlocks = 64;   // fixed partition of the observables reduction
 struct ObsArgs {
     int R, kind;
+    const int* Rdev;             // population in device memory (or null: R)
     const int32_t* E32;
     const longlong2* E128;
     const int32_t* family;

@@ -130,7 +130,7 @@ extern "C" int pa_resample_static(const int32_t* d_E, int R, double beta_prev, d
     }
     cudaStream_t st = (cudaStream_t)stream;
     static_prep_kernel<<<1, 1024, 0, st>>>(d_E, R, base);
-    pa::ResampleArgs ra;
+    pa::ResampleArgs ra{};
     ra.R = R;
     ra.Rn = R;
     ra.kind = 0;

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(WARPS * 32) sweep_real_kernel(RealSweepArgs a)
     extern __shared__ __align__(16) unsigned char smem_real[];
     const bool grad = a.i.cJ != nullptr;
     real_stage<D, L, WARPS>(a.i, smem_real, grad);
-    const int ntiles = (a.i.R + 31) / 32;
+    const int ntiles = ((a.i.Rdev ? __ldg(a.i.Rdev) : a.i.R) + 31) / 32;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
         sweep_real_tile<D, L, WARPS>(a.s, a.i, tile, smem_real, grad);
     if (grad) real_flush_grad<D, L, WARPS>(a.i, smem_real);

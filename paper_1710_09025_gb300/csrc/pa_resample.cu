@@ -29,12 +29,16 @@ __device__ __forceinline__ double e_minus_min_to_double(const ResampleArgs& a, i
     return __dmul_rn(i128_to_double(ll2_to_i128(a.E128[i]) - emin), 0x1p-96);
 }
 
+// source population: in device memory for the nearest-integer scheme
+__device__ __forceinline__ int rs_src(const ResampleArgs& a) { return a.Rsrc ? *a.Rsrc : a.R; }
+
 // weights and chunk-local sequential prefix sums (one block per chunk)
 __device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int c)
 {
     __shared__ double wsh[kChunk];
     const int i0 = c * kChunk;
-    const int n = min(kChunk, a.R - i0);
+    const int n = min(kChunk, rs_src(a) - i0);
+    if (n <= 0) return;  // block-uniform
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const double d = e_minus_min_to_double(a, i0 + t);
         const double w = spec_exp64(-__dmul_rn(a.dbeta, d));
@@ -57,13 +61,14 @@ __global__ void __launch_bounds__(256) rs_weights_kernel(ResampleArgs a) { rs_we
 __global__ void __launch_bounds__(256) rs_weights_batched(const ResampleArgs* tab)
 {
     const ResampleArgs& a = tab[blockIdx.y];
-    if ((int)blockIdx.x * kChunk < a.R) rs_weights_body(a, blockIdx.x);
+    rs_weights_body(a, blockIdx.x);
 }
 
 // chunk offsets (sequential), S, ln Q, running free energy
 __device__ __forceinline__ void rs_offsets_body(const ResampleArgs& a)
 {
-    const int nchunks = (a.R + kChunk - 1) / kChunk;
+    const int R = rs_src(a);
+    const int nchunks = (R + kChunk - 1) / kChunk;
     double T = 0.0;
     for (int c = 0; c < nchunks; ++c) {
         a.T[c] = T;
@@ -78,7 +83,8 @@ __device__ __forceinline__ void rs_offsets_body(const ResampleArgs& a)
         __int128 emin = ((__int128)a.prev->emin_hi << 64) | (unsigned long long)a.prev->emin_lo;
         emin_d = __dmul_rn(i128_to_double(emin), 0x1p-96);
     }
-    const double lnQ = __dsub_rn(__dadd_rn(-__dmul_rn(a.dbeta, emin_d), log(S)), a.log_R);
+    const double log_R = a.Rsrc ? log((double)R) : a.log_R;
+    const double lnQ = __dsub_rn(__dadd_rn(-__dmul_rn(a.dbeta, emin_d), log(S)), log_R);
     const double sum = __dadd_rn(a.prev->sum_lnQ, lnQ);
     a.cur->lnQ = lnQ;
     a.cur->sum_lnQ = sum;
@@ -97,7 +103,7 @@ __global__ void rs_offsets_batched(const ResampleArgs* tab, int n_inst)
 
 __device__ __forceinline__ void rs_finalize_body(const ResampleArgs& a, int i)
 {
-    if (i < a.R) a.P[i] = __dadd_rn(a.T[i / kChunk], a.P[i]);
+    if (i < rs_src(a)) a.P[i] = __dadd_rn(a.T[i / kChunk], a.P[i]);
 }
 __global__ void rs_finalize_kernel(ResampleArgs a) { rs_finalize_body(a, blockIdx.x * blockDim.x + threadIdx.x); }
 __global__ void rs_finalize_batched(const ResampleArgs* tab)
@@ -134,6 +140,23 @@ __global__ void rs_draws_batched(const ResampleArgs* tab)
     rs_draws_body(tab[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// nearest-integer copy numbers (Sec. II.B, population in expectation):
+// tau_i = target w_i / S, n_i = floor(tau_i) + [u_i < tau_i - floor(tau_i)],
+// u_i from the RESAMPLE stream at counter (i, k, 1)
+__device__ __forceinline__ void rs_nearest_body(const ResampleArgs& a, int i)
+{
+    const int R = rs_src(a);
+    if (i >= R) return;
+    const int nchunks = (R + kChunk - 1) / kChunk;
+    const double S = a.T[nchunks];
+    const u32x4 o = philox((uint32_t)i, (uint32_t)a.k, 1u, a.c3, a.key0, a.key1);
+    const double u = uniform53(o.x, o.y);
+    const double tau = __ddiv_rn(__dmul_rn(a.target, a.w[i]), S);
+    const double fl = floor(tau);
+    a.counts[i] = (int32_t)fl + (u < __dsub_rn(tau, fl) ? 1 : 0);
+}
+__global__ void rs_nearest_kernel(ResampleArgs a) { rs_nearest_body(a, blockIdx.x * blockDim.x + threadIdx.x); }
+
 __device__ __forceinline__ void rs_blocksum_body(const int32_t* counts, int R, int32_t* blocksum, int b)
 {
     __shared__ int ws[32];
@@ -151,9 +174,10 @@ __device__ __forceinline__ void rs_blocksum_body(const int32_t* counts, int R, i
         if (tid == 0) blocksum[b] = v;
     }
 }
-__global__ void __launch_bounds__(1024) rs_blocksum_kernel(const int32_t* counts, int R, int32_t* blocksum)
+__global__ void __launch_bounds__(1024) rs_blocksum_kernel(ResampleArgs a)
 {
-    rs_blocksum_body(counts, R, blocksum, blockIdx.x);
+    const int R = rs_src(a);
+    if ((int)blockIdx.x * kScanBlock < R) rs_blocksum_body(a.counts, R, a.blocksum, blockIdx.x);
 }
 __global__ void __launch_bounds__(1024) rs_blocksum_batched(const ResampleArgs* tab)
 {
@@ -161,7 +185,7 @@ __global__ void __launch_bounds__(1024) rs_blocksum_batched(const ResampleArgs* 
     if ((int)blockIdx.x * kScanBlock < a.R) rs_blocksum_body(a.counts, a.R, a.blocksum, blockIdx.x);
 }
 
-__device__ __forceinline__ void rs_scan_blocks_body(int32_t* blocksum, int nb)
+__device__ __forceinline__ int rs_scan_blocks_body(int32_t* blocksum, int nb)
 {
     int acc = 0;
     for (int b = 0; b < nb; ++b) {
@@ -169,10 +193,18 @@ __device__ __forceinline__ void rs_scan_blocks_body(int32_t* blocksum, int nb)
         blocksum[b] = acc;
         acc += v;
     }
+    return acc;
 }
-__global__ void rs_scan_blocks_kernel(int32_t* blocksum, int nb)
+__global__ void rs_scan_blocks_kernel(ResampleArgs a)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) rs_scan_blocks_body(blocksum, nb);
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int R = rs_src(a);
+    const int total = rs_scan_blocks_body(a.blocksum, (R + kScanBlock - 1) / kScanBlock);
+    if (a.Rdst) {  // the drawn population, copies beyond the capacity dropped
+        const int Rn = min(total, a.cap);
+        *a.Rdst = Rn;
+        *a.Rdst_d = (double)Rn;
+    }
 }
 __global__ void rs_scan_blocks_batched(const ResampleArgs* tab, int n_inst)
 {
@@ -190,8 +222,10 @@ __device__ __forceinline__ void rs_fill_body(const ResampleArgs& a, int b)
     int c[PER];
     int s = 0;
 #pragma unroll
+    const int R = rs_src(a);
+    const int cap = a.Rdst ? a.cap : 0x7fffffff;
     for (int t = 0; t < PER; ++t) {
-        c[t] = (i0 + t < a.R) ? a.counts[i0 + t] : 0;
+        c[t] = (i0 + t < R) ? a.counts[i0 + t] : 0;
         s += c[t];
     }
     int incl = s;
@@ -217,9 +251,10 @@ __device__ __forceinline__ void rs_fill_body(const ResampleArgs& a, int b)
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
         const int i = i0 + t;
-        if (i < a.R) {
+        if (i < R) {
             const int f = a.fam_in[i];
-            for (int u = 0; u < c[t]; ++u) {
+            const int n = min(c[t], max(cap - off, 0));  // slots past the capacity are dropped
+            for (int u = 0; u < n; ++u) {
                 a.parent[off + u] = i;
                 a.fam_out[off + u] = f;
             }
@@ -228,7 +263,10 @@ __device__ __forceinline__ void rs_fill_body(const ResampleArgs& a, int b)
         }
     }
 }
-__global__ void __launch_bounds__(1024) rs_fill_kernel(ResampleArgs a) { rs_fill_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(1024) rs_fill_kernel(ResampleArgs a)
+{
+    if ((int)blockIdx.x * kScanBlock < rs_src(a)) rs_fill_body(a, blockIdx.x);
+}
 __global__ void __launch_bounds__(1024) rs_fill_batched(const ResampleArgs* tab)
 {
     const ResampleArgs& a = tab[blockIdx.y];
@@ -242,9 +280,12 @@ cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
     rs_weights_kernel<<<nchunks, 256, 0, st>>>(a);
     rs_offsets_kernel<<<1, 32, 0, st>>>(a);
     rs_finalize_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
-    rs_draws_kernel<<<(a.Rn + 255) / 256, 256, 0, st>>>(a);
-    rs_blocksum_kernel<<<nb, 1024, 0, st>>>(a.counts, a.R, a.blocksum);
-    rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a.blocksum, nb);
+    if (a.scheme == 1)
+        rs_nearest_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
+    else
+        rs_draws_kernel<<<(a.Rn + 255) / 256, 256, 0, st>>>(a);
+    rs_blocksum_kernel<<<nb, 1024, 0, st>>>(a);
+    rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a);
     rs_fill_kernel<<<nb, 1024, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -274,8 +315,9 @@ __device__ __forceinline__ void observe_partial_body(const ObsArgs& a)
     __shared__ double s_d[3][32];
     __shared__ __int128 s_min[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (a.R + kObsBlocks - 1) / kObsBlocks;
-    const int j0 = blockIdx.x * per, j1 = min(a.R, j0 + per);
+    const int R = a.Rdev ? *a.Rdev : a.R;
+    const int per = (R + kObsBlocks - 1) / kObsBlocks;
+    const int j0 = blockIdx.x * per, j1 = min(R, j0 + per);
     long long se = 0, se2 = 0;
     double sed = 0.0, se2d = 0.0, clnc = 0.0;
     __int128 mn = (__int128)(((unsigned __int128)1 << 127) - 1);
@@ -295,7 +337,7 @@ __device__ __forceinline__ void observe_partial_body(const ObsArgs& a)
         }
         const int f = a.family[j];
         if (j == 0 || a.family[j - 1] != f) {
-            int lo = j + 1, hi = a.R;  // first index with family > f (families are sorted)
+            int lo = j + 1, hi = R;  // first index with family > f (families are sorted)
             while (lo < hi) {
                 const int mid = lo + ((hi - lo) >> 1);
                 if (a.family[mid] > f) hi = mid; else lo = mid + 1;

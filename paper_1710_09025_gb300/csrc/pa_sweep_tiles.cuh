@@ -127,7 +127,9 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     uint8_t* sj = smem + SH::TILE;
     uint64_t* cnt = reinterpret_cast<uint64_t*>(smem + SH::TILE + SH::SJ);
 
-    const int G = in.G, R = in.R;
+    const int R = in.Rdev ? __ldg(in.Rdev) : in.R;
+    const int G = in.Rdev ? (R + 63) >> 6 : in.G;
+    if (g0 >= G) return;  // block-uniform: past the population held in device memory
     const uint32_t c3 = in.c3;
     const int32_t* __restrict__ parent = in.parent;
     const int ng = min(GPB, G - g0);
@@ -488,7 +490,7 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
     int* gh = gJ + D * N;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int R = in.R, NP = in.NP;
+    const int R = in.Rdev ? __ldg(in.Rdev) : in.R, NP = in.NP;
     const uint32_t c3 = in.c3;
     const int nchunk = NP / 16;
     const int r0 = tile * 32;

@@ -80,6 +80,42 @@ def test_option_validation(lib):
     assert rc == -1 and "packed" in msg
 
 
+def test_resampling_option_validation(lib):
+    import paper_1710_09025_gb300 as P
+    P.load(lib._name)
+    o = P.pa_options_default(resampling=2)
+    rc, out, msg = _create(lib, opt=o)
+    assert rc == -1 and "resampling" in msg
+    o = P.pa_options_default(capacity=-1)
+    rc, out, msg = _create(lib, opt=o)
+    assert rc == -1 and "capacity" in msg
+    o = P.pa_options_default(resampling=1, capacity=5)
+    rc, out, msg = _create(lib, R=10, opt=o)
+    assert rc == -1 and "capacity" in msg
+    o = P.pa_options_default(populations=[10, 12])  # multinomial: at most R
+    rc, out, msg = _create(lib, R=10, opt=o)
+    assert rc == -1 and "populations" in msg
+    o = P.pa_options_default(resampling=1, populations=[10, 200], capacity=100)
+    rc, out, msg = _create(lib, R=10, opt=o)
+    assert rc == -1 and "populations" in msg
+
+
+def test_options_struct_matches_the_header(tmp_path):
+    """ctypes' pa_options has the size and field offsets of the C struct."""
+    import paper_1710_09025_gb300 as P
+    names = [f[0] for f in P.pa_options._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pa.h"\nint main(void) {\n'
+                   '  printf("%zu", sizeof(pa_options));\n' +
+                   "".join(f'  printf(" %zu", offsetof(pa_options, {n}));\n' for n in names) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(P.pa_options)
+    assert got[1:] == [getattr(P.pa_options, n).offset for n in names]
+
+
 def test_workspace_size_is_positive_and_grows_with_R(lib):
     import paper_1710_09025_gb300 as P
     P.load(lib._name)
