@@ -180,6 +180,17 @@ int pa_get_family(pa_ctx* ctx, int32_t* host_family /* R: initial ancestor of sl
 int pa_get_grad_counts(pa_ctx* ctx, int64_t* host_cJ, int64_t* host_ch);
 int pa_sizes(const pa_ctx* ctx, int* D, int* L, int* N, int* R, int* n_temps, int* layout);
 
+/* Checkpoint / resume.  A checkpoint is the state the next step reads (the
+ * spins in use, energies, parents, families, per-temperature accumulators,
+ * populations, gradient counts) behind a header that pins the configuration.
+ * pa_checkpoint_save (synchronises) writes pa_checkpoint_size() bytes to a
+ * host buffer; pa_checkpoint_load restores them into a context created with
+ * the same arguments and options (PA_EINVAL otherwise), after which the run
+ * continues exactly as the saved one would have. */
+int pa_checkpoint_size(const pa_ctx* ctx, size_t* bytes);
+int pa_checkpoint_save(pa_ctx* ctx, void* host_buf, size_t bytes);
+int pa_checkpoint_load(pa_ctx* ctx, const void* host_buf, size_t bytes);
+
 /* Per-phase timing with CUDA events recorded on the context's stream around
  * each phase of pa_anneal_step (off by default; not recorded inside pa_anneal
  * graphs).  Phases: 0 init, 1 resampling (weights..parents), 2 replica gather,

@@ -91,6 +91,9 @@ def load(path: str | None = None):
             "pa_get_family": (i32, [vp, vp]),
             "pa_get_grad_counts": (i32, [vp, vp, vp]),
             "pa_sizes": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]),
+            "pa_checkpoint_size": (i32, [vp, P(sz)]),
+            "pa_checkpoint_save": (i32, [vp, vp, sz]),
+            "pa_checkpoint_load": (i32, [vp, vp, sz]),
             "pa_profile": (i32, [vp, i32]),
             "pa_phase_times": (i32, [vp, vp, vp, vp]),
             "pa_resample_static": (i32, [vp, i32, ctypes.c_double, ctypes.c_double, i32, u64,
@@ -280,6 +283,19 @@ def pa_get_family(ctx) -> np.ndarray:
     return out
 
 
+def pa_checkpoint_save(ctx) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(load().pa_checkpoint_size(ctx, ctypes.byref(n)), ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().pa_checkpoint_save(ctx, buf, n.value), ctx)
+    return buf.raw
+
+
+def pa_checkpoint_load(ctx, data: bytes):
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(load().pa_checkpoint_load(ctx, buf, len(data)), ctx)
+
+
 def pa_get_grad_counts(ctx):
     s = pa_sizes(ctx)
     cJ = np.empty((s["n_temps"], s["D"] * s["N"]), np.int64)
@@ -409,6 +425,14 @@ class Population:
 
     def observables(self, k):
         return pa_observables(self.ctx, k)
+
+    def save(self) -> bytes:
+        """Checkpoint of the run's state (synchronises)."""
+        return pa_checkpoint_save(self.ctx)
+
+    def load(self, data: bytes):
+        """Resume from a checkpoint of a run with the same arguments."""
+        pa_checkpoint_load(self.ctx, data)
 
     def close(self):
         if self.ctx:

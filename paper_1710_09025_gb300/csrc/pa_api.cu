@@ -883,6 +883,138 @@ extern "C" int pa_sizes(const pa_ctx* c, int* D, int* L, int* N, int* R, int* n_
     return PA_OK;
 }
 
+// ---------------- checkpoint / resume ----------------
+//
+// A checkpoint holds the state that the next step reads: the spin buffer in
+// use, energies, parents, families, the per-temperature accumulators, the
+// populations and (with accumulate_grad) the gradient counts, behind a
+// header that pins the configuration (sizes, options, seed, and an FNV-1a
+// fingerprint of the couplings, field, schedule and population targets).
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t D, L, kind, cap, n_temps, n_sweeps, layout, scheme, acc_grad;
+    uint32_t inst, tag;
+    uint64_t seed, fingerprint;
+    int32_t k_next, cur, famcur, pad;
+};
+constexpr char kCkptMagic[8] = {'P', 'A', 'M', 'C', 'C', 'K', 'P', 'T'};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n)
+{
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+struct CkptSection {
+    void* dev;
+    size_t bytes;
+};
+}  // namespace
+
+static std::vector<CkptSection> ckpt_sections(pa_ctx* c)
+{
+    std::vector<CkptSection> v;
+    const size_t cap = (size_t)c->R;
+    if (c->layout == PA_LAYOUT_PACKED) v.push_back({c->S[c->cur], sizeof(uint64_t) * (size_t)c->G * c->N});
+    else v.push_back({c->S8[c->cur], cap * c->NP});
+    if (c->kind == PA_PM1) v.push_back({c->E32, sizeof(int32_t) * cap});
+    else v.push_back({c->E128, sizeof(longlong2) * cap});
+    v.push_back({c->parent, sizeof(int32_t) * cap});
+    v.push_back({c->fam[c->famcur], sizeof(int32_t) * cap});
+    v.push_back({c->acc, sizeof(StepAcc) * c->n_temps});
+    v.push_back({c->Rdev, sizeof(int) * c->n_temps});
+    v.push_back({c->Rk_d, sizeof(double) * c->n_temps});
+    if (c->acc_grad) {
+        v.push_back({c->cJ, sizeof(unsigned long long) * (size_t)c->n_temps * c->D * c->N});
+        v.push_back({c->ch, sizeof(unsigned long long) * (size_t)c->n_temps * c->N});
+    }
+    return v;
+}
+
+static CkptHeader ckpt_header(const pa_ctx* c)
+{
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.D = c->D; h.L = c->L; h.kind = c->kind; h.cap = c->R; h.n_temps = c->n_temps;
+    h.n_sweeps = c->n_sweeps; h.layout = c->layout; h.scheme = c->scheme; h.acc_grad = c->acc_grad;
+    h.inst = c->inst; h.tag = c->tag; h.seed = c->seed;
+    uint64_t f = 1469598103934665603ull;
+    f = fnv1a(f, c->Jh.data(), sizeof(float) * c->Jh.size());
+    f = fnv1a(f, c->hh.data(), sizeof(float) * c->hh.size());
+    f = fnv1a(f, c->betas.data(), sizeof(double) * c->betas.size());
+    f = fnv1a(f, c->Rk.data(), sizeof(int) * c->Rk.size());
+    h.fingerprint = f;
+    h.k_next = c->k_next; h.cur = c->cur; h.famcur = c->famcur;
+    return h;
+}
+
+extern "C" int pa_checkpoint_size(const pa_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return PA_EINVAL;
+    size_t n = sizeof(CkptHeader);
+    for (const auto& sct : ckpt_sections(const_cast<pa_ctx*>(c))) n += sct.bytes;
+    *bytes = n;
+    return PA_OK;
+}
+
+extern "C" int pa_checkpoint_save(pa_ctx* c, void* buf, size_t bytes)
+{
+    if (!c || !buf) return PA_EINVAL;
+    size_t need = 0;
+    pa_checkpoint_size(c, &need);
+    if (bytes < need) { c->err = "checkpoint buffer too small"; return PA_EINVAL; }
+    const CkptHeader h = ckpt_header(c);
+    std::memcpy(buf, &h, sizeof h);
+    char* p = (char*)buf + sizeof h;
+    for (const auto& sct : ckpt_sections(c)) {
+        PA_CK(c, cudaMemcpyAsync(p, sct.dev, sct.bytes, cudaMemcpyDeviceToHost, c->st));
+        p += sct.bytes;
+    }
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    return PA_OK;
+}
+
+extern "C" int pa_checkpoint_load(pa_ctx* c, const void* buf, size_t bytes)
+{
+    if (!c || !buf) return PA_EINVAL;
+    CkptHeader h;
+    if (bytes < sizeof h) { c->err = "checkpoint truncated"; return PA_EINVAL; }
+    std::memcpy(&h, buf, sizeof h);
+    CkptHeader mine = ckpt_header(c);
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) { c->err = "not a checkpoint"; return PA_EINVAL; }
+    mine.k_next = h.k_next; mine.cur = h.cur; mine.famcur = h.famcur;
+    if (std::memcmp(&h, &mine, sizeof h) != 0) {
+        c->err = "checkpoint of a different configuration (sizes, options, seed, couplings or schedule)";
+        return PA_EINVAL;
+    }
+    if (h.k_next < 0 || h.k_next > c->n_temps || (h.cur & ~1) || (h.famcur & ~1)) {
+        c->err = "checkpoint state out of range";
+        return PA_EINVAL;
+    }
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    c->k_next = h.k_next; c->cur = h.cur; c->famcur = h.famcur;
+    size_t need = 0;
+    pa_checkpoint_size(c, &need);
+    if (bytes < need) { c->err = "checkpoint truncated"; return PA_EINVAL; }
+    const char* p = (const char*)buf + sizeof h;
+    for (const auto& sct : ckpt_sections(c)) {
+        PA_CK(c, cudaMemcpyAsync(sct.dev, p, sct.bytes, cudaMemcpyHostToDevice, c->st));
+        p += sct.bytes;
+    }
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    return PA_OK;
+}
+
 extern "C" int pa_profile(pa_ctx* c, int enable)
 {
     if (!c) return PA_EINVAL;
