@@ -34,7 +34,8 @@ extern "C" {
 enum { OR_PM1 = 0, OR_REAL = 1 };
 
 /* Philox stream ids (bits 28..31 of counter word 3). */
-enum { OR_STREAM_INIT = 1, OR_STREAM_PLANE = 2, OR_STREAM_WORD = 3, OR_STREAM_RESAMPLE = 4 };
+enum { OR_STREAM_INIT = 1, OR_STREAM_PLANE = 2, OR_STREAM_WORD = 3, OR_STREAM_RESAMPLE = 4,
+       OR_STREAM_ICM = 5 };
 
 /* ---- primitives (philox.c, specmath.c) ---- */
 void     or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -81,6 +82,17 @@ or_sim* or_create_ex(int D, int L, int kind, const float* J, const float* h, int
                      const double* betas, int n_temps, int n_sweeps, uint64_t seed,
                      uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad,
                      const int32_t* populations, int scheme, int capacity);
+/* isoenergetic cluster moves (Sec. III.C): at steps k >= 1 with
+ * icm_beta_lo <= beta_k <= icm_beta_hi (hi <= 0: every such step), N_S/2
+ * sweeps, two rounds of ICM updates on disjoint random pairs (R updates),
+ * then the remaining sweeps.  Needs a zero field. */
+int     or_set_icm(or_sim* s, int enable, double icm_beta_lo, double icm_beta_hi);
+/* the random pairing: the permutation pi_t of [0, n) of ICM round t at step k */
+uint32_t or_icm_perm(uint32_t i, uint32_t n, int k, int t, uint64_t seed, uint32_t inst, uint32_t tag);
+/* one ICM update of replicas a and b (int8 rows of N spins, modified in
+ * place) with the 32-bit site-choice word r32; returns the island size
+ * (0: no update) */
+int     or_icm_pair(int D, int L, int8_t* a, int8_t* b, uint32_t r32);
 int     or_current_R(const or_sim* s);
 void    or_destroy(or_sim* s);
 /* runs temperature index k = next step; returns k, -1 after the last one, -2

@@ -73,6 +73,9 @@ def lib():
                 "or_create_ex": (vp, [i32, i32, i32, vp, vp, i32, vp, i32, i32, u64, u32, u32, i32, vp,
                                       i32, i32]),
                 "or_default_capacity": (i32, [i32]),
+                "or_set_icm": (i32, [vp, i32, dbl, dbl]),
+                "or_icm_perm": (u32, [u32, u32, i32, i32, u64, u32, u32]),
+                "or_icm_pair": (i32, [i32, i32, vp, vp, u32]),
                 "or_resample_nearest": (i32, [i32, i32, vp, dbl, dbl, i32, u64, u32, u32, dbl, i32,
                                               vp, vp, vp, vp, vp]),
                 "or_current_R": (i32, [vp]),
@@ -214,6 +217,19 @@ def resample_nearest(kind, E_pairs, beta_prev, beta_next, k, seed, target, cap, 
     return dict(w=w, P=P, parent=parent[:Rn], counts=counts, lnQ=lnQ.value, Rn=Rn)
 
 
+def icm_perm(i, n, k, t, seed, inst=0, tag=0):
+    """pi_t(i): the random pairing permutation of [0, n) (Sec. III.C)."""
+    return lib().or_icm_perm(int(i), int(n), int(k), int(t), int(seed), int(inst), int(tag))
+
+
+def icm_pair(D, L, a, b, r32):
+    """One isoenergetic cluster move on int8 rows a, b: (a', b', island size)."""
+    a = np.ascontiguousarray(a, dtype=np.int8).copy()
+    b = np.ascontiguousarray(b, dtype=np.int8).copy()
+    n = lib().or_icm_pair(D, L, _p(a), _p(b), int(r32))
+    return a, b, n
+
+
 def default_capacity(R_max):
     return lib().or_default_capacity(int(R_max))
 
@@ -255,7 +271,8 @@ class Sim:
     MULTINOMIAL, NEAREST = 0, 1
 
     def __init__(self, D, L, kind, J, h, R, betas, n_sweeps, seed, rng_instance=0, rng_tag=0,
-                 accumulate_grad=False, populations=None, resampling=0, capacity=0):
+                 accumulate_grad=False, populations=None, resampling=0, capacity=0, icm=False,
+                 icm_beta=(0.0, 0.0)):
         self.D, self.L, self.kind, self.R = D, L, kind, R
         self.N = L ** D
         self.betas = np.ascontiguousarray(betas, dtype=np.float64)
@@ -270,6 +287,8 @@ class Sim:
                                      int(capacity))
         if not self._h:
             raise ValueError("oracle rejected the configuration")
+        if icm and lib().or_set_icm(self._h, 1, float(icm_beta[0]), float(icm_beta[1])) != 0:
+            raise ValueError("cluster moves need a zero field")
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -48,6 +48,8 @@ struct or_sim {
     int D, L, N, kind, R, G, n_temps, n_sweeps, k_next, acc_grad;
     int Rcap, R_src_last;      /* capacity; source population of the last resampling */
     int scheme, dead;          /* resampling scheme; population died out */
+    int icm;                   /* isoenergetic cluster moves (Sec. III.C) */
+    double icm_lo, icm_hi;     /* beta window of the cluster moves */
     int32_t* Rk;               /* population at each temperature (Sec. III.D, Eq. 6) */
     uint64_t seed;
     uint32_t inst, tag;
@@ -220,6 +222,21 @@ static void halfsweep_real(const lat_ctx* c, int8_t* s, int r0, int nrep, double
     }
 }
 
+/* sweeps sw0 .. sw1-1 of the n_sweeps at step k (half-sweep index
+ * hs = 2 (k n_sweeps + sw) + parity whatever the split) */
+static void sweeps_range(const lat_ctx* c, int kind, int8_t* s, int r0, int nrep, double beta, int k,
+                         int n_sweeps, int sw0, int sw1)
+{
+    for (int sw = sw0; sw < sw1; ++sw)
+        for (int p = 0; p < 2; ++p) {
+            int hs = 2 * (k * n_sweeps + sw) + p;
+            if (kind == OR_PM1)
+                halfsweep_pm(c, s, r0, nrep, beta, hs, p);
+            else
+                halfsweep_real(c, s, r0, nrep, beta, hs, p);
+        }
+}
+
 static void sweeps(const lat_ctx* c, int kind, int8_t* s, int r0, int nrep, double beta, int k,
                    int n_sweeps)
 {
@@ -231,6 +248,122 @@ static void sweeps(const lat_ctx* c, int kind, int8_t* s, int r0, int nrep, doub
             else
                 halfsweep_real(c, s, r0, nrep, beta, hs, p);
         }
+}
+
+/* ---------------- isoenergetic cluster moves (Sec. III.C) ----------------
+ *
+ * Two replicas a, b: the overlap q_i = S^a_i S^b_i splits the lattice into
+ * islands (connected sets of sites of equal q).  One island is drawn from
+ * the sector (q = -1 or q = +1) with fewer sites (ties: q = -1), its spins
+ * are flipped in both replicas; E_a + E_b is unchanged for a zero field, so
+ * the move is always accepted.  The island is the lattice-connected
+ * component, in that sector, of the idx-th sector site in site order,
+ * idx = floor(r32 n_sector / 2^32).
+ *
+ * Random pairing: round t of step k pairs pi_t(2i) with pi_t(2i+1),
+ * i < floor(R/2), where pi_t is a 4-round Feistel permutation of
+ * [0, 2^m) (m even, the smallest with 2^m >= R, at least 2) walked in
+ * cycles back into [0, R): halves of m/2 bits, (Lh, Rh) -> (Rh, Lh ^ F_j(Rh)),
+ * F_j(v) = out0 of Philox at counter (v, k, 4t + j, ICM stream) masked to
+ * m/2 bits.  The site-choice word of pair i in round t is out0 at counter
+ * (i, k, 16 + t, ICM stream). */
+
+static uint32_t icm_feistel(uint32_t x, int h, int k, int t, const uint32_t key[2], uint32_t c3)
+{
+    const uint32_t mask = (h >= 32) ? 0xFFFFFFFFu : ((1u << h) - 1u);
+    uint32_t Lh = (x >> h) & mask, Rh = x & mask;
+    for (int j = 0; j < 4; ++j) {
+        uint32_t ctr[4] = {Rh, (uint32_t)k, (uint32_t)(4 * t + j), c3}, out[4];
+        or_philox4x32_10(ctr, key, out);
+        uint32_t nl = Rh, nr = Lh ^ (out[0] & mask);
+        Lh = nl;
+        Rh = nr;
+    }
+    return (Lh << h) | Rh;
+}
+
+uint32_t or_icm_perm(uint32_t i, uint32_t n, int k, int t, uint64_t seed, uint32_t inst, uint32_t tag)
+{
+    int m = 2;
+    while (m < 32 && (1ull << m) < (unsigned long long)n) m += 2;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t c3 = or_counter3(OR_STREAM_ICM, tag, inst);
+    uint32_t y = icm_feistel(i, m / 2, k, t, key, c3);
+    while (y >= n) y = icm_feistel(y, m / 2, k, t, key, c3);
+    return y;
+}
+
+int or_icm_pair(int D, int L, int8_t* a, int8_t* b, uint32_t r32)
+{
+    int N = ipow(L, D);
+    int32_t* nbr = (int32_t*)malloc(sizeof(int32_t) * (size_t)N * 2 * D);
+    int32_t* bond = (int32_t*)malloc(sizeof(int32_t) * (size_t)N * 2 * D);
+    or_lattice(D, L, nbr, bond);
+    int nneg = 0;
+    for (int i = 0; i < N; ++i) nneg += (a[i] * b[i] < 0);
+    int sigma = (nneg <= N - nneg) ? -1 : 1;
+    int nsec = sigma < 0 ? nneg : N - nneg;
+    int size = 0;
+    if (nsec > 0) {
+        uint32_t idx = (uint32_t)(((uint64_t)r32 * (uint64_t)nsec) >> 32);
+        int c = -1;
+        for (int i = 0, seen = 0; i < N; ++i)
+            if (a[i] * b[i] == sigma) {
+                if ((uint32_t)seen == idx) { c = i; break; }
+                ++seen;
+            }
+        /* breadth-first search of the island of c */
+        int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+        uint8_t* in = (uint8_t*)calloc((size_t)N, 1);
+        int head = 0, tail = 0;
+        queue[tail++] = c;
+        in[c] = 1;
+        while (head < tail) {
+            int i = queue[head++];
+            for (int nb = 0; nb < 2 * D; ++nb) {
+                int j = nbr[i * 2 * D + nb];
+                if (!in[j] && a[j] * b[j] == sigma) {
+                    in[j] = 1;
+                    queue[tail++] = j;
+                }
+            }
+        }
+        for (int q = 0; q < tail; ++q) {
+            a[queue[q]] = (int8_t)-a[queue[q]];
+            b[queue[q]] = (int8_t)-b[queue[q]];
+        }
+        size = tail;
+        free(queue);
+        free(in);
+    }
+    free(nbr);
+    free(bond);
+    return size;
+}
+
+static void icm_rounds(or_sim* s, int k)
+{
+    uint32_t key[2] = {(uint32_t)s->seed, (uint32_t)(s->seed >> 32)};
+    uint32_t c3 = or_counter3(OR_STREAM_ICM, s->tag, s->inst);
+    for (int t = 0; t < 2; ++t)
+        for (int i = 0; i < s->R / 2; ++i) {
+            uint32_t pa_ = or_icm_perm((uint32_t)(2 * i), (uint32_t)s->R, k, t, s->seed, s->inst, s->tag);
+            uint32_t pb_ = or_icm_perm((uint32_t)(2 * i + 1), (uint32_t)s->R, k, t, s->seed, s->inst, s->tag);
+            uint32_t ctr[4] = {(uint32_t)i, (uint32_t)k, (uint32_t)(16 + t), c3}, out[4];
+            or_philox4x32_10(ctr, key, out);
+            or_icm_pair(s->D, s->L, s->s + (size_t)pa_ * s->N, s->s + (size_t)pb_ * s->N, out[0]);
+        }
+}
+
+int or_set_icm(or_sim* s, int enable, double icm_beta_lo, double icm_beta_hi)
+{
+    if (enable && s->h)
+        for (int i = 0; i < s->N; ++i)
+            if (s->h[i] != 0.0f) return -1; /* the moves conserve energy only without a field */
+    s->icm = enable ? 1 : 0;
+    s->icm_lo = icm_beta_lo;
+    s->icm_hi = icm_beta_hi;
+    return 0;
 }
 
 /* ---------------- energies (Eq. 1 plus field) ---------------- */
@@ -621,7 +754,15 @@ int or_step(or_sim* s)
         int32_t* f = s->family; s->family = s->family_tmp; s->family_tmp = f;
     }
     lat_ctx c = lat_of(s);
-    sweeps(&c, s->kind, s->s, 0, s->R, s->betas[k], k, s->n_sweeps);
+    const double beta = s->betas[k];
+    if (s->icm && k > 0 && beta >= s->icm_lo && (s->icm_hi <= 0.0 || beta <= s->icm_hi)) {
+        const int h1 = s->n_sweeps / 2;
+        sweeps_range(&c, s->kind, s->s, 0, s->R, beta, k, s->n_sweeps, 0, h1);
+        icm_rounds(s, k);
+        sweeps_range(&c, s->kind, s->s, 0, s->R, beta, k, s->n_sweeps, h1, s->n_sweeps);
+    } else {
+        sweeps(&c, s->kind, s->s, 0, s->R, beta, k, s->n_sweeps);
+    }
     measure(s, k, lnQ);
     s->k_next = k + 1;
     return k;
