@@ -31,6 +31,9 @@ struct pa_ctx {
     std::vector<double> betas;
     std::vector<int> Rk;        // population (target) at each temperature; R = capacity
     int scheme;                 // PA_RESAMPLE_*; nearest-integer: populations in Rdev
+    int icm;                    // isoenergetic cluster moves and their beta window
+    double icm_lo, icm_hi;
+    int* icm_err;               // device flag: a bounded union-find loop gave up
     int* Rdev;                  // [n_temps] populations in device memory
     std::vector<float> Jh, hh;  // flushed host copies
     // device
@@ -134,7 +137,7 @@ struct Layout {
 enum {
     W_J, W_H, W_JNEG, W_JFIX, W_HFIX, W_BETAS, W_S0, W_S1, W_E32, W_E128, W_PARENT, W_FAM0, W_FAM1,
     W_COUNTS, W_BLOCKSUM, W_W, W_P, W_TOT, W_T, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
-    W_DH, W_OBSPART, W_RK, W_RDEV, W_COUNT
+    W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_COUNT
 };
 
 static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps, int acc_grad)
@@ -175,6 +178,7 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
     sz[W_OBSPART] = sizeof(pa::ObsPartial) * pa::kObsBlocks;
     sz[W_RK] = sizeof(double) * n_temps;
     sz[W_RDEV] = sizeof(int) * n_temps;
+    sz[W_ICMERR] = sizeof(int);
     Layout lay;
     size_t off = 0;
     for (int i = 0; i < W_COUNT; ++i) {
@@ -253,6 +257,16 @@ static int validate(std::string& err, int D, int L, int kind, const float* J, co
             return PA_EINVAL;
         }
         if (o->capacity < 0) { err = "capacity must be >= 0"; return PA_EINVAL; }
+        if (o->icm) {
+            if (h)
+                for (int i = 0; i < N; ++i)
+                    if (h[i] != 0.0f) { err = "cluster moves (icm) need a zero field"; return PA_EINVAL; }
+            if (!std::isfinite(o->icm_beta_lo) || !std::isfinite(o->icm_beta_hi)) {
+                err = "icm beta window must be finite";
+                return PA_EINVAL;
+            }
+            if (N > 4096) { err = "cluster moves support N <= 4096"; return PA_EINVAL; }
+        }
         const long long cap = capacity_of(R, n_temps, o);
         if (cap > (1 << 26)) { err = "capacity must be <= 2^26"; return PA_EINVAL; }
         if (o->resampling == PA_RESAMPLE_NEAREST && !o->populations && cap < R) {
@@ -315,7 +329,8 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     pa_ctx* c = new pa_ctx();
     const int cap = (int)capacity_of(R, n_temps, &o);
     c->D = D; c->L = L; c->N = (D == 3) ? L * L * L : L * L; c->kind = kind; c->R = cap;
-    c->G = (cap + 63) / 64; c->scheme = o.resampling; c->n_temps = n_temps; c->n_sweeps = n_sweeps; c->k_next = 0;
+    c->G = (cap + 63) / 64; c->scheme = o.resampling;
+    c->icm = o.icm ? 1 : 0; c->icm_lo = o.icm_beta_lo; c->icm_hi = o.icm_beta_hi; c->n_temps = n_temps; c->n_sweeps = n_sweeps; c->k_next = 0;
     c->layout = resolve_layout(kind, &o); c->NP = (c->N + 15) / 16 * 16;
     c->seed = seed; c->inst = o.rng_instance; c->tag = o.rng_tag; c->acc_grad = o.accumulate_grad ? 1 : 0;
     c->st = (cudaStream_t)stream;
@@ -394,6 +409,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->obspart = (pa::ObsPartial*)at(W_OBSPART);
     c->Rk_d = (double*)at(W_RK);
     c->Rdev = (int*)at(W_RDEV);
+    c->icm_err = (int*)at(W_ICMERR);
 
     // couplings: sign masks (+-J), fixed-point copies (real)
     std::vector<uint8_t> jn(N, 0);
@@ -434,6 +450,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     if (rc2 == PA_OK) {
         cudaError_t e = cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * (size_t)R, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(StepAcc) * n_temps, c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->icm_err, 0, sizeof(int), c->st);
         if (e == cudaSuccess && c->acc_grad) {
             e = cudaMemsetAsync(c->cJ, 0, sizeof(unsigned long long) * (size_t)n_temps * D * N, c->st);
             if (e == cudaSuccess) e = cudaMemsetAsync(c->ch, 0, sizeof(unsigned long long) * (size_t)n_temps * N, c->st);
@@ -474,6 +491,7 @@ static void fill_packed_step(pa::PackedStep* s, int D, double beta, int k, int n
     std::memset(s, 0, sizeof *s);
     s->k = k;
     s->n_sweeps = n_sweeps;
+    s->hs0 = 2u * (uint32_t)(k * n_sweeps);
     uint32_t thr[4] = {0, 0, 0, 0};
     for (int cl = 1; cl <= 3; ++cl) {
         const uint64_t t = pa::threshold_pm(beta, 4 * cl);
@@ -510,6 +528,12 @@ struct StepPlan {
     pa::ResampleArgs rs;       // k > 0
     pa::PackedSweepArgs pk;    // PA_PM1
     pa::RealSweepArgs re;      // PA_REAL
+    // cluster moves: pk / re run the first N_S/2 sweeps, then two rounds of
+    // moves, then pk2 / re2 the remaining sweeps (no gather, in place)
+    bool icm;
+    pa::IcmArgs ic;
+    pa::PackedSweepArgs pk2;
+    pa::RealSweepArgs re2;
     pa::ObsArgs ob;
     // context state after the step
     int cur, famcur;
@@ -546,8 +570,12 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         ra.key0 = k0; ra.key1 = k1; ra.c3 = pa::counter3(pa::STREAM_RES, c->tag, c->inst);
         c->famcur ^= 1;
     }
+    const bool icm = c->icm && k > 0 && beta >= c->icm_lo && (c->icm_hi <= 0.0 || beta <= c->icm_hi);
+    const int h1 = c->n_sweeps / 2;
+    pl->icm = icm;
     if (c->kind == PA_PM1) {
         fill_packed_step(&pl->pk.s, c->D, beta, k, c->n_sweeps, k0, k1);
+        if (icm) pl->pk.s.n_sweeps = h1;
         pa::PackedInst& in = pl->pk.i;
         in.jneg = c->jneg; in.E = c->E32; in.G = G; in.R = R; in.NP = c->NP;
         if (dyn) { in.Rdev = c->Rdev + k; in.G = c->G; in.R = c->R; }
@@ -565,9 +593,22 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
             in.parent = k > 0 ? c->parent : nullptr;
             c->cur ^= 1;
         }
+        if (icm) {
+            pl->pk2 = pl->pk;
+            pl->pk2.s.n_sweeps = c->n_sweeps - h1;
+            pl->pk2.s.hs0 = 2u * (uint32_t)(k * c->n_sweeps + h1);
+            pa::PackedInst& i2 = pl->pk2.i;
+            i2.parent = nullptr;
+            if (c->layout == PA_LAYOUT_PACKED) {
+                i2.Sin = c->S[c->cur]; i2.S = c->S[c->cur];  // in place
+            } else {
+                i2.S8_in = c->S8[c->cur]; i2.S8_out = c->S8[c->cur ^ 1];
+            }
+        }
     } else {
         pa::RealStep& st = pl->re.s;
-        st.k = k; st.n_sweeps = c->n_sweeps; st.beta = (float)beta; st.key0 = k0; st.key1 = k1;
+        st.k = k; st.n_sweeps = icm ? h1 : c->n_sweeps; st.beta = (float)beta; st.key0 = k0; st.key1 = k1;
+        st.hs0 = 2u * (uint32_t)(k * c->n_sweeps);
         pa::RealInst& in = pl->re.i;
         in.Sin = c->S8[c->cur]; in.Sout = c->S8[c->cur ^ 1];
         in.parent = k > 0 ? c->parent : nullptr;
@@ -577,6 +618,27 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         in.R = R; in.NP = c->NP; in.c3 = pa::counter3(pa::STREAM_WORD, c->tag, c->inst);
         if (dyn) { in.Rdev = c->Rdev + k; in.R = c->R; }
         c->cur ^= 1;
+        if (icm) {
+            pl->re2 = pl->re;
+            pl->re2.s.n_sweeps = c->n_sweeps - h1;
+            pl->re2.s.hs0 = 2u * (uint32_t)(k * c->n_sweeps + h1);
+            in.cJ = nullptr; in.ch = nullptr;  // counts after the last sweep only
+            pa::RealInst& i2 = pl->re2.i;
+            i2.parent = nullptr;
+            i2.Sin = c->S8[c->cur]; i2.Sout = c->S8[c->cur ^ 1];
+        }
+    }
+    if (icm) {
+        pa::IcmArgs& ic = pl->ic;
+        ic.D = c->D; ic.L = c->L; ic.N = c->N; ic.NP = c->NP;
+        if (c->layout == PA_LAYOUT_PACKED) { ic.S = c->S[c->cur]; ic.S8 = nullptr; }
+        else { ic.S = nullptr; ic.S8 = c->S8[c->cur]; }
+        ic.Rdev = dyn ? c->Rdev + k : nullptr;
+        ic.R = dyn ? c->R : R;
+        ic.k = k; ic.t = 0;
+        ic.key0 = k0; ic.key1 = k1; ic.c3 = pa::counter3(pa::STREAM_ICM, c->tag, c->inst);
+        ic.err = c->icm_err;
+        if (c->layout != PA_LAYOUT_PACKED || c->kind == PA_REAL) c->cur ^= 1;  // the second sweep launch ping-pongs
     }
     pa::ObsArgs& oa = pl->ob;
     oa.R = R; oa.kind = c->kind == PA_PM1 ? 0 : 1; oa.E32 = c->E32; oa.E128 = c->E128;
@@ -630,6 +692,18 @@ static int enqueue_step(pa_ctx* c)
     else
         PA_CK(c, pa::launch_sweep_real(c->D, c->L, pl.re, c->real_warps, 0, c->st));
     c->launches += 1;
+    if (pl.icm) {
+        for (int t = 0; t < 2; ++t) {
+            pa::IcmArgs ic = pl.ic;
+            ic.t = t;
+            PA_CK(c, pa::launch_icm(ic, c->st));
+        }
+        if (c->kind == PA_PM1)
+            PA_CK(c, pa::launch_sweep_packed(c->D, c->L, pl.pk2, c->gpb, c->threads, c->st));
+        else
+            PA_CK(c, pa::launch_sweep_real(c->D, c->L, pl.re2, c->real_warps, 0, c->st));
+        c->launches += 3;
+    }
     phase_end(c, PA_PHASE_SWEEP, ev);
     ev = phase_begin(c);
     PA_CK(c, pa::launch_observe(pl.ob, c->st));
@@ -718,6 +792,11 @@ extern "C" int pa_synchronize(pa_ctx* c)
 {
     if (!c) return PA_EINVAL;
     PA_CK(c, cudaStreamSynchronize(c->st));
+    if (c->icm) {
+        int bad = 0;
+        PA_CK(c, cudaMemcpy(&bad, c->icm_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (bad) { c->err = "a cluster-move union-find loop reached its bound"; return PA_ETIMEOUT; }
+    }
     int R;
     return pop_now(c, &R);  // PA_EEMPTY once the population died out
 }
@@ -949,6 +1028,8 @@ static CkptHeader ckpt_header(const pa_ctx* c)
     f = fnv1a(f, c->hh.data(), sizeof(float) * c->hh.size());
     f = fnv1a(f, c->betas.data(), sizeof(double) * c->betas.size());
     f = fnv1a(f, c->Rk.data(), sizeof(int) * c->Rk.size());
+    const double icmw[3] = {(double)c->icm, c->icm_lo, c->icm_hi};
+    f = fnv1a(f, icmw, sizeof icmw);
     h.fingerprint = f;
     h.k_next = c->k_next; h.cur = c->cur; h.famcur = c->famcur;
     return h;
@@ -1144,7 +1225,7 @@ extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_
     if (D != 3) { g_create_err = "batched sweeps support D = 3"; return PA_EINVAL; }
     if (n_inst < 1 || !descs) { g_create_err = "need at least one instance"; return PA_EINVAL; }
     if (opt && (opt->layout != PA_LAYOUT_AUTO || opt->accumulate_grad || opt->populations ||
-                opt->resampling != PA_RESAMPLE_MULTINOMIAL || opt->capacity)) {
+                opt->resampling != PA_RESAMPLE_MULTINOMIAL || opt->capacity || opt->icm)) {
         g_create_err = "batch: layout must be AUTO, accumulate_grad 0, populations NULL, multinomial "
                        "resampling and no capacity";
         return PA_EINVAL;
@@ -1306,6 +1387,7 @@ static void batch_step_params(pa_batch* b, int k, pa::PackedStep* ps, pa::RealSt
     const uint32_t k0 = (uint32_t)b->seed, k1 = (uint32_t)(b->seed >> 32);
     fill_packed_step(ps, b->D, b->betas[k], k, b->n_sweeps, k0, k1);
     rs->k = k; rs->n_sweeps = b->n_sweeps; rs->beta = (float)b->betas[k]; rs->key0 = k0; rs->key1 = k1;
+    rs->hs0 = 2u * (uint32_t)(k * b->n_sweeps);
 }
 
 // time every candidate sweep configuration on step k; a sweep with k >= 1

@@ -28,7 +28,7 @@
 
 namespace pa {
 
-enum : uint32_t { STREAM_INIT = 1, STREAM_PLANE = 2, STREAM_WORD = 3, STREAM_RES = 4 };
+enum : uint32_t { STREAM_INIT = 1, STREAM_PLANE = 2, STREAM_WORD = 3, STREAM_RES = 4, STREAM_ICM = 5 };
 
 PA_HD uint32_t counter3(uint32_t stream, uint32_t tag, uint32_t instance)
 {

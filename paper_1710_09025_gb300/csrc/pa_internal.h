@@ -22,7 +22,8 @@ static_assert(sizeof(StepAcc) == 96, "StepAcc layout");
 // ---------------- packed +-J path ----------------
 // Parameters of one temperature, uniform over every instance of a launch.
 struct PackedStep {
-    int k, n_sweeps;
+    int k, n_sweeps;         // n_sweeps: sweeps of this launch
+    uint32_t hs0;            // half-sweep index of its first half-sweep, 2 (k N_S + first sweep)
     int mode;                // undecided uphill classes: 1 = {dE=4}, 2 = {dE=4, dE=8}, 0 = any set
     uint32_t und;            // bit c: class c (dE = 4c) needs a random comparison (0 < thr < 2^32)
     uint32_t always;         // bit c: class c always accepted (thr == 2^32)
@@ -62,7 +63,8 @@ cudaError_t launch_overlap_packed(const uint64_t* A, const uint64_t* B, int N, i
 
 // ---------------- int8 path ----------------
 struct RealStep {
-    int k, n_sweeps;
+    int k, n_sweeps;         // n_sweeps: sweeps of this launch
+    uint32_t hs0;            // 2 (k N_S + first sweep)
     float beta;
     uint32_t key0, key1;
 };
@@ -106,6 +108,19 @@ cudaError_t batch_sweep_occupancy(size_t smem, int* blocks_per_sm);
 cudaError_t launch_sweep_batched(const PackedStep& ps, const RealStep& rs, const BatchSweepInst* insts,
                                  const int2* items, int n_items, int mult, int* counter, int blocks,
                                  size_t smem, cudaStream_t st);
+
+// ---------------- isoenergetic cluster moves (Sec. III.C) ----------------
+struct IcmArgs {
+    int D, L, N, NP;
+    uint64_t* S;             // packed words [G][N] (or null)
+    int8_t* S8;              // int8 rows [R][NP] (or null)
+    const int* Rdev;         // population in device memory (or null: R)
+    int R;                   // population, or the capacity with Rdev
+    int k, t;                // step, round (0 or 1)
+    uint32_t key0, key1, c3; // Philox key, counter word 3 of the ICM stream
+    int* err;                // set if a bounded union-find loop gave up
+};
+cudaError_t launch_icm(const IcmArgs& a, cudaStream_t st);
 
 // ---------------- resampling and observables ----------------
 struct ResampleArgs {

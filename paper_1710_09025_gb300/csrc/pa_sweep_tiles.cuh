@@ -205,7 +205,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     const int xh_c = (tid % NH) % LT::LH, y_c = ((tid % NH) / LT::LH) % L;
     for (int sw = 0; sw < s.n_sweeps; ++sw) {
         for (int p = 0; p < 2; ++p) {
-            const uint32_t hs = 2u * (uint32_t)(s.k * s.n_sweeps + sw) + (uint32_t)p;
+            const uint32_t hs = s.hs0 + 2u * (uint32_t)sw + (uint32_t)p;
             // neighbour decoding: when every item of this thread sits on the same
             // sublattice site (THREADS a multiple of N/2) decode once; when it sits
             // on the same x-y column (3D, THREADS a multiple of L^2/2) only z moves
@@ -516,7 +516,7 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
     // ---- N_S sweeps
     for (int sw = 0; sw < s.n_sweeps; ++sw) {
         for (int p = 0; p < 2; ++p) {
-            const uint32_t hsw = 2u * (uint32_t)(s.k * s.n_sweeps + sw) + (uint32_t)p;
+            const uint32_t hsw = s.hs0 + 2u * (uint32_t)sw + (uint32_t)p;
             const int8_t* oth = T + (p ^ 1) * NH * 32;
             int8_t* cur = T + p * NH * 32;
             for (int blk = warp; blk < NB; blk += WARPS) {
