@@ -518,6 +518,7 @@ static void fill_packed_step(pa::PackedStep* s, int D, double beta, int k, int n
         s->v00[b] = bit(cls_n0);
         s->v01[b] = bit(cls_n1);
         s->v10[b] = bit(cls_n2);
+        if ((s->v00[b] | s->v01[b] | s->v10[b]) == 0) s->zero_planes |= 1u << b;
     }
 }
 

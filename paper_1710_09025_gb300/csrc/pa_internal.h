@@ -32,6 +32,7 @@ struct PackedStep {
     // two low bits (b1 b0) of the unsatisfied-bond count n of an uphill lane:
     // v00: n = 0, v01: n = 1, v10: n = 2
     uint32_t v00[32], v01[32], v10[32];
+    uint32_t zero_planes;    // bit b: every threshold bit of plane b is 0 (a 1 in r rejects)
 };
 // Parameters of one instance.
 struct PackedInst {

@@ -269,19 +269,39 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     };
     auto compare_mode02 = [&](uint32_t q, uint32_t g, uint32_t hs, uint64_t U, uint64_t b0, uint64_t b1,
                               uint64_t& acc) {
+        // planes where every threshold bit is 0 only reject (a 1 in r decides
+        // r > thr): one masking step instead of the class selection
+        const uint32_t zp = s.zero_planes;
         if (s.mode == 2) {
             const uint64_t sel = (D == 3) ? b1 : b0;  // 1 selects the dE = 4 class
 #pragma unroll
             for (int m = 0; m < 16; ++m) {
                 if (!U) break;
                 const u32x4 o = philox_rk(q, hs, 16u * g + (uint32_t)m, c3, s.rk);
-                plane_step_two((uint64_t)o.x | ((uint64_t)o.y << 32), (D == 3) ? s.v10[2 * m] : s.v01[2 * m],
-                               (D == 3) ? s.v01[2 * m] : s.v00[2 * m], sel, U, acc);
-                plane_step_two((uint64_t)o.z | ((uint64_t)o.w << 32),
-                               (D == 3) ? s.v10[2 * m + 1] : s.v01[2 * m + 1],
-                               (D == 3) ? s.v01[2 * m + 1] : s.v00[2 * m + 1], sel, U, acc);
+                const uint64_t p0 = (uint64_t)o.x | ((uint64_t)o.y << 32);
+                const uint64_t p1 = (uint64_t)o.z | ((uint64_t)o.w << 32);
+                if ((zp >> (2 * m)) & 1u) U &= ~p0;
+                else plane_step_two(p0, (D == 3) ? s.v10[2 * m] : s.v01[2 * m],
+                                    (D == 3) ? s.v01[2 * m] : s.v00[2 * m], sel, U, acc);
+                if ((zp >> (2 * m + 1)) & 1u) U &= ~p1;
+                else plane_step_two(p1, (D == 3) ? s.v10[2 * m + 1] : s.v01[2 * m + 1],
+                                    (D == 3) ? s.v01[2 * m + 1] : s.v00[2 * m + 1], sel, U, acc);
+            }
+        } else if ((zp & 3u) == 3u) {
+            // thresholds below 2^30: leading planes only reject
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                if (!U) break;
+                const u32x4 o = philox_rk(q, hs, 16u * g + (uint32_t)m, c3, s.rk);
+                const uint64_t p0 = (uint64_t)o.x | ((uint64_t)o.y << 32);
+                const uint64_t p1 = (uint64_t)o.z | ((uint64_t)o.w << 32);
+                if ((zp >> (2 * m)) & 1u) U &= ~p0;
+                else plane_step(p0, s.v00[2 * m], s.v01[2 * m], s.v10[2 * m], b0, b1, U, acc);
+                if ((zp >> (2 * m + 1)) & 1u) U &= ~p1;
+                else plane_step(p1, s.v00[2 * m + 1], s.v01[2 * m + 1], s.v10[2 * m + 1], b0, b1, U, acc);
             }
         } else {
+            // high temperature: threshold bits of 1 from the first planes on
 #pragma unroll
             for (int m = 0; m < 16; ++m) {
                 if (!U) break;
