@@ -94,7 +94,8 @@ struct PackedShape {
     static constexpr size_t TILE = (size_t)GPB * 2 * NH * 8;
     static constexpr size_t SJ = ((size_t)N + 15) / 16 * 16;
     static constexpr size_t CNT = (size_t)GPB * NSEG * B * 8;
-    static constexpr size_t QUEUE = 16 + (size_t)THREADS * (3 * 8 + 4);  // mode-1 queue of undecided words
+    static constexpr int QIPT = 4;  // mode-1 items per thread per queue round
+    static constexpr size_t QUEUE = 32 + (size_t)QIPT * THREADS * (8 + 4);  // mode-1 queue of undecided words
     static constexpr size_t SMEM = TILE + SJ + CNT + QUEUE;
     static_assert(THREADS % GPB == 0 && (TPG & (TPG - 1)) == 0, "threads per group");
 };
@@ -333,12 +334,12 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
             U = (m1 & und1) | (m2 & und2) | (m3 & und3);
         }
     };
-    int* qn = reinterpret_cast<int*>(qbuf);  // two round counters, then the queue
-    uint64_t* QU = reinterpret_cast<uint64_t*>(qbuf + 16);
-    uint64_t* Qacc = QU + THREADS;
-    uint64_t* Qsw = Qacc + THREADS;
-    int* Qt = reinterpret_cast<int*>(Qsw + THREADS);
-    if (tid < 2) qn[tid] = 0;
+    // mode-1 queue: per round two counters (entries, next entry to take), then
+    // the undecided masks and item indices
+    int* qn = reinterpret_cast<int*>(qbuf);
+    uint64_t* QU = reinterpret_cast<uint64_t*>(qbuf + 32);
+    int* Qt = reinterpret_cast<int*>(QU + SH::QIPT * THREADS);
+    if (tid < 4) qn[tid] = 0;
     __syncthreads();
     int round = 0;
     // compaction pays only in mode 1 (measured at L=16: mode 1 steps 14.5 ->
@@ -354,35 +355,40 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                 // Words with undecided lanes are compacted into a block queue so
                 // that the comparison loop runs on full warps: at low temperature
                 // most words have no dE = 4 lane, the others need several planes.
-                for (int base = 0; base < ng * NH; base += THREADS, ++round) {
-                    const int t = base + tid;
-                    uint64_t U = 0, acc = 0, sw0 = 0, b0 = 0, b1 = 0;
-                    if (t < ng * NH) {
-                        uint64_t* cur;
-                        int q;
-                        uint64_t b2, down;
-                        classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
-                        acc = down;  // no uphill class is always accepted in mode 1
-                        U = ~down & ((D == 3) ? b1 : b0);
-                        if (!U) cur[q] = sw0 ^ acc;
-                    }
-                    int* cnt_r = qn + (round & 1);
-                    const unsigned bal = __ballot_sync(0xffffffffu, U != 0);
-                    int wb = 0;
-                    if (lane == 0 && bal) wb = atomicAdd(cnt_r, __popc(bal));
-                    wb = __shfl_sync(0xffffffffu, wb, 0);
-                    if (U) {
-                        const int slot = wb + __popc(bal & ((1u << lane) - 1u));
-                        QU[slot] = U; Qacc[slot] = acc; Qsw[slot] = sw0; Qt[slot] = t;
+                // Lanes with dE <= 0 are flipped at once; the queue entries, taken
+                // one at a time by whichever thread is free, add the accepted ones.
+                for (int base = 0; base < ng * NH; base += SH::QIPT * THREADS, ++round) {
+                    int* cnt_r = qn + 2 * (round & 1);
+#pragma unroll
+                    for (int it = 0; it < SH::QIPT; ++it) {
+                        const int t = base + it * THREADS + tid;
+                        uint64_t U = 0;
+                        if (t < ng * NH) {
+                            uint64_t* cur;
+                            int q;
+                            uint64_t sw0, b0, b1, b2, down;
+                            classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
+                            cur[q] = sw0 ^ down;  // no uphill class is always accepted in mode 1
+                            U = ~down & ((D == 3) ? b1 : b0);
+                        }
+                        const unsigned bal = __ballot_sync(0xffffffffu, U != 0);
+                        int wb = 0;
+                        if (lane == 0 && bal) wb = atomicAdd(cnt_r, __popc(bal));
+                        wb = __shfl_sync(0xffffffffu, wb, 0);
+                        if (U) {
+                            const int slot = wb + __popc(bal & ((1u << lane) - 1u));
+                            QU[slot] = U;
+                            Qt[slot] = t;
+                        }
                     }
                     __syncthreads();
-                    const int n = *cnt_r;
-                    if (tid == 0) qn[(round + 1) & 1] = 0;  // the next round's counter
-                    if (tid < n) {
-                        const int t2 = Qt[tid], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
-                        uint64_t acc2 = Qacc[tid];
-                        compare_mode1((uint32_t)q2, (uint32_t)(g0 + gl2), hs, QU[tid], acc2);
-                        sm[(gl2 * 2 + p) * NH + q2] = Qsw[tid] ^ acc2;
+                    const int n = cnt_r[0];
+                    if (tid == 0) { qn[2 * ((round + 1) & 1)] = 0; qn[2 * ((round + 1) & 1) + 1] = 0; }
+                    for (int e = atomicAdd(cnt_r + 1, 1); e < n; e = atomicAdd(cnt_r + 1, 1)) {
+                        const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
+                        uint64_t acc2 = 0;
+                        compare_mode1((uint32_t)q2, (uint32_t)(g0 + gl2), hs, QU[e], acc2);
+                        sm[(gl2 * 2 + p) * NH + q2] ^= acc2;
                     }
                     __syncthreads();
                 }
