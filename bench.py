@@ -300,7 +300,7 @@ def run_gpu(args, wl_name):
         v, n, dt = oracle_rate(D, L, J, R_s, sb, ns, w["seed"], kind=kind, h=h)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{wl_name} lattice and couplings, R'={R_s} replicas, "
-                                          f"beta in {list(sb)}, N_S={ns}: {n} steps in {dt:.1f} s"}
+                                          f"beta in {[round(float(x), 4) for x in sb]}, N_S={ns}: {n} steps in {dt:.1f} s"}
     if ws > 1:
         torch.distributed.destroy_process_group()
     print(json.dumps(line))
