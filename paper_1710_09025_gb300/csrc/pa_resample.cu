@@ -64,16 +64,28 @@ __global__ void __launch_bounds__(256) rs_weights_batched(const ResampleArgs* ta
     rs_weights_body(a, blockIdx.x);
 }
 
-// chunk offsets (sequential), S, ln Q, running free energy
+// chunk offsets (sequential), S, ln Q, running free energy.  One warp: the
+// chunk sums are staged in shared memory 1024 at a time (coalesced loads),
+// lane 0 adds them in chunk order.
 __device__ __forceinline__ void rs_offsets_body(const ResampleArgs& a)
 {
+    __shared__ double tsh[1024];
+    const int lane = threadIdx.x & 31;
     const int R = rs_src(a);
     const int nchunks = (R + kChunk - 1) / kChunk;
     double T = 0.0;
-    for (int c = 0; c < nchunks; ++c) {
-        a.T[c] = T;
-        T = __dadd_rn(T, a.tot[c]);
+    for (int c0 = 0; c0 < nchunks; c0 += 1024) {
+        const int n = min(1024, nchunks - c0);
+        for (int c = lane; c < n; c += 32) tsh[c] = a.tot[c0 + c];
+        __syncwarp();
+        if (lane == 0)
+            for (int c = 0; c < n; ++c) {
+                a.T[c0 + c] = T;
+                T = __dadd_rn(T, tsh[c]);
+            }
+        __syncwarp();
     }
+    if (lane != 0) return;
     a.T[nchunks] = T;
     const double S = T;
     double emin_d;
@@ -93,12 +105,13 @@ __device__ __forceinline__ void rs_offsets_body(const ResampleArgs& a)
 }
 __global__ void rs_offsets_kernel(ResampleArgs a)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) rs_offsets_body(a);
+    if (threadIdx.x < 32 && blockIdx.x == 0) rs_offsets_body(a);
 }
+// one warp per instance
 __global__ void rs_offsets_batched(const ResampleArgs* tab, int n_inst)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_inst) rs_offsets_body(tab[i]);
+    const int i = blockIdx.x;
+    if (i < n_inst && threadIdx.x < 32) rs_offsets_body(tab[i]);
 }
 
 __device__ __forceinline__ void rs_finalize_body(const ResampleArgs& a, int i)
@@ -296,7 +309,7 @@ cudaError_t launch_resample_batched(const ResampleArgs* tab, int n_inst, int max
     const unsigned nb = (maxR + kScanBlock - 1) / kScanBlock;
     const unsigned ni = (unsigned)n_inst;
     rs_weights_batched<<<dim3(nchunks, ni), 256, 0, st>>>(tab);
-    rs_offsets_batched<<<(ni + 63) / 64, 64, 0, st>>>(tab, n_inst);
+    rs_offsets_batched<<<ni, 32, 0, st>>>(tab, n_inst);
     rs_finalize_batched<<<dim3((maxR + 255) / 256, ni), 256, 0, st>>>(tab);
     rs_draws_batched<<<dim3((maxR + 255) / 256, ni), 256, 0, st>>>(tab);
     rs_blocksum_batched<<<dim3(nb, ni), 1024, 0, st>>>(tab);
