@@ -439,6 +439,9 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     // ---- energies: vertical counters of unsatisfied bonds ----
     {
         const int gl = tid / TPG, lt = tid - gl * TPG;
+        // a thread counts at most ceil(N / TPG) sites of D bonds each
+        constexpr int W = bits_for(((N + TPG - 1) / TPG) * D) > 2 ? bits_for(((N + TPG - 1) / TPG) * D) : 2;
+        static_assert(W <= B, "per-thread counter fits the block counter");
         uint64_t C[B];
 #pragma unroll
         for (int b = 0; b < B; ++b) C[b] = 0;
@@ -453,17 +456,26 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                 nbs[0] = i - x + (x == L - 1 ? 0 : x + 1);
                 nbs[1] = i + ((y == L - 1) ? -(L - 1) * L : L);
                 if (D == 3) nbs[2] = i + ((z == L - 1) ? -(L - 1) * L * L : L * L);
+                uint64_t ub[3] = {0, 0, 0};  // unsatisfied +e_d bonds of site i
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
                     const int j = nbs[d];
                     const uint64_t sjw = base[(p ^ 1) * NH + (j >> 1)];
-                    uint64_t carry = si ^ sjw ^ (((jm >> (2 * d + 1)) & 1u) ? ~0ull : 0ull);
+                    ub[d] = si ^ sjw ^ (((jm >> (2 * d + 1)) & 1u) ? ~0ull : 0ull);
+                }
+                // the site's count (0..D) as two bit-sliced bits, added into the
+                // thread's counter, whose width W covers this thread's sites only
+                const uint64_t lo = ub[0] ^ ub[1] ^ ub[2], hi = maj3(ub[0], ub[1], ub[2]);
+                uint64_t carry = C[0] & lo;
+                C[0] ^= lo;
+                uint64_t c2 = maj3(C[1], hi, carry);
+                C[1] ^= hi ^ carry;
+                carry = c2;
 #pragma unroll
-                    for (int b = 0; b < B; ++b) {
-                        uint64_t tt = C[b] & carry;
-                        C[b] ^= carry;
-                        carry = tt;
-                    }
+                for (int b = 2; b < W; ++b) {
+                    const uint64_t tt = C[b] & carry;
+                    C[b] ^= carry;
+                    carry = tt;
                 }
             }
         }
