@@ -12,6 +12,8 @@
 #include "pa_device.cuh"
 #include "pa_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -73,9 +75,15 @@ struct pa_ctx {
     long long launches;
 };
 
+// NVTX range names of the phases (host-side ranges around each phase's
+// launches, for timeline and kernel-filter tools; no-ops without a tool)
+static const char* const kPhaseName[PA_NPHASE] = {"pa/init", "pa/resample", "pa/gather", "pa/sweep",
+                                                   "pa/observe"};
+
 // records the start of a phase; returns the start event (or null)
-static cudaEvent_t phase_begin(pa_ctx* c)
+static cudaEvent_t phase_begin(pa_ctx* c, int phase)
 {
+    nvtxRangePushA(kPhaseName[phase]);
     if (!c->profiling || c->capturing) return nullptr;
     cudaEvent_t e;
     if (!c->ev_free.empty()) { e = c->ev_free.back(); c->ev_free.pop_back(); }
@@ -86,6 +94,7 @@ static cudaEvent_t phase_begin(pa_ctx* c)
 
 static void phase_end(pa_ctx* c, int phase, cudaEvent_t start)
 {
+    nvtxRangePop();
     if (!start) return;
     cudaEvent_t e;
     if (!c->ev_free.empty()) { e = c->ev_free.back(); c->ev_free.pop_back(); }
@@ -674,7 +683,7 @@ static int enqueue_step(pa_ctx* c)
     if (k >= c->n_temps) { c->err = "schedule finished"; return PA_EDONE; }
     cudaEvent_t ev;
     if (k == 0) {
-        ev = phase_begin(c);
+        ev = phase_begin(c, PA_PHASE_INIT);
         int rc = enqueue_init(c);
         if (rc) return rc;
         phase_end(c, PA_PHASE_INIT, ev);
@@ -682,12 +691,12 @@ static int enqueue_step(pa_ctx* c)
     StepPlan pl;
     plan_step(c, &pl);
     if (k > 0) {
-        ev = phase_begin(c);
+        ev = phase_begin(c, PA_PHASE_RESAMPLE);
         PA_CK(c, pa::launch_resample(pl.rs, c->st));
         c->launches += 7;
         phase_end(c, PA_PHASE_RESAMPLE, ev);
     }
-    ev = phase_begin(c);
+    ev = phase_begin(c, PA_PHASE_SWEEP);
     if (c->kind == PA_PM1)
         PA_CK(c, pa::launch_sweep_packed(c->D, c->L, pl.pk, c->gpb, c->threads, c->st));
     else
@@ -706,7 +715,7 @@ static int enqueue_step(pa_ctx* c)
         c->launches += 3;
     }
     phase_end(c, PA_PHASE_SWEEP, ev);
-    ev = phase_begin(c);
+    ev = phase_begin(c, PA_PHASE_OBSERVE);
     PA_CK(c, pa::launch_observe(pl.ob, c->st));
     c->launches += 2;
     phase_end(c, PA_PHASE_OBSERVE, ev);
