@@ -36,6 +36,7 @@ struct pa_ctx {
     int icm;                    // isoenergetic cluster moves and their beta window
     double icm_lo, icm_hi;
     int* icm_err;               // device flag: a bounded union-find loop gave up
+    double* wtab;               // +-J: resampling weight per energy level
     int* Rdev;                  // [n_temps] populations in device memory
     std::vector<float> Jh, hh;  // flushed host copies
     // device
@@ -146,7 +147,7 @@ struct Layout {
 enum {
     W_J, W_H, W_JNEG, W_JFIX, W_HFIX, W_BETAS, W_S0, W_S1, W_E32, W_E128, W_PARENT, W_FAM0, W_FAM1,
     W_COUNTS, W_BLOCKSUM, W_W, W_P, W_TOT, W_T, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
-    W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_COUNT
+    W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_WTAB, W_COUNT
 };
 
 static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps, int acc_grad)
@@ -188,6 +189,7 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
     sz[W_RK] = sizeof(double) * n_temps;
     sz[W_RDEV] = sizeof(int) * n_temps;
     sz[W_ICMERR] = sizeof(int);
+    sz[W_WTAB] = kind == PA_PM1 ? sizeof(double) * (size_t)(D * N / 2 + 1) : 0;
     Layout lay;
     size_t off = 0;
     for (int i = 0; i < W_COUNT; ++i) {
@@ -419,6 +421,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->Rk_d = (double*)at(W_RK);
     c->Rdev = (int*)at(W_RDEV);
     c->icm_err = (int*)at(W_ICMERR);
+    c->wtab = kind == PA_PM1 ? (double*)at(W_WTAB) : nullptr;
 
     // couplings: sign masks (+-J), fixed-point copies (real)
     std::vector<uint8_t> jn(N, 0);
@@ -577,6 +580,7 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         ra.fam_in = c->fam[c->famcur]; ra.fam_out = c->fam[c->famcur ^ 1];
         ra.dbeta = c->betas[k] - c->betas[k - 1];
         ra.log_R = std::log((double)Rprev); ra.betaF0 = c->betaF0; ra.k = k;
+        ra.wtab = c->wtab; ra.wtab_n = c->wtab ? c->D * c->N / 2 + 1 : 0;  // E - E_min <= 2 D N
         ra.key0 = k0; ra.key1 = k1; ra.c3 = pa::counter3(pa::STREAM_RES, c->tag, c->inst);
         c->famcur ^= 1;
     }
@@ -693,7 +697,7 @@ static int enqueue_step(pa_ctx* c)
     if (k > 0) {
         ev = phase_begin(c, PA_PHASE_RESAMPLE);
         PA_CK(c, pa::launch_resample(pl.rs, c->st));
-        c->launches += 7;
+        c->launches += pl.rs.wtab ? 8 : 7;
         phase_end(c, PA_PHASE_RESAMPLE, ev);
     }
     ev = phase_begin(c, PA_PHASE_SWEEP);
@@ -1317,6 +1321,8 @@ extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_
             plan_step(c, &pl);
             const size_t at = (size_t)k * n_inst + i;
             rs[at] = pl.rs;
+            rs[at].wtab = nullptr;  // the batched resampling computes every weight
+            rs[at].wtab_n = 0;
             std::memset(&sw[at], 0, sizeof sw[at]);
             sw[at].cls = cls;
             sw[at].pk = pl.pk.i;

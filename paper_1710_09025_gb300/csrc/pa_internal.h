@@ -139,6 +139,8 @@ struct ResampleArgs {
     const StepAcc* prev;         // acc[k-1]: E_min, sum_lnQ
     StepAcc* cur;                // acc[k]: lnQ, sum_lnQ, betaF, S
     double* w;                   // [R] weights
+    const double* wtab;          // +-J: weight per level (E - E_min) / 4, or null
+    int wtab_n;                  // levels in wtab
     double* P;                   // [R] local prefix, then P
     double* tot;                 // [nchunks] chunk sums
     double* T;                   // [nchunks + 1] chunk offsets

@@ -40,8 +40,14 @@ __device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int c)
     const int n = min(kChunk, rs_src(a) - i0);
     if (n <= 0) return;  // block-uniform
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const double d = e_minus_min_to_double(a, i0 + t);
-        const double w = spec_exp64(-__dmul_rn(a.dbeta, d));
+        double w;
+        const int lv = a.kind == 0 ? a.E32[i0 + t] - (int)a.prev->emin_lo : 0;
+        if (a.wtab && (lv & 3) == 0 && (lv >> 2) < a.wtab_n) {
+            w = a.wtab[lv >> 2];  // +-J: E - E_min is a multiple of 4, the weight a table entry
+        } else {
+            const double d = e_minus_min_to_double(a, i0 + t);
+            w = spec_exp64(-__dmul_rn(a.dbeta, d));
+        }
         wsh[t] = w;
         a.w[i0 + t] = w;
     }
@@ -62,6 +68,15 @@ __global__ void __launch_bounds__(256) rs_weights_batched(const ResampleArgs* ta
 {
     const ResampleArgs& a = tab[blockIdx.y];
     rs_weights_body(a, blockIdx.x);
+}
+
+// +-J: all energies are congruent modulo 4 (Delta E of a flip is 4D - 4n),
+// so E - E_min takes the values 4l, l < wtab_n; the weight of level l,
+// spec_exp64(-(dbeta * 4l)), is the same arithmetic as for a replica
+__global__ void rs_table_kernel(ResampleArgs a)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < a.wtab_n) const_cast<double*>(a.wtab)[l] = spec_exp64(-__dmul_rn(a.dbeta, (double)(4 * l)));
 }
 
 // chunk offsets (sequential), S, ln Q, running free energy.  One warp: the
@@ -290,6 +305,7 @@ cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
 {
     const int nchunks = (a.R + kChunk - 1) / kChunk;
     const int nb = (a.R + kScanBlock - 1) / kScanBlock;
+    if (a.wtab) rs_table_kernel<<<(a.wtab_n + 255) / 256, 256, 0, st>>>(a);
     rs_weights_kernel<<<nchunks, 256, 0, st>>>(a);
     rs_offsets_kernel<<<1, 32, 0, st>>>(a);
     rs_finalize_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
