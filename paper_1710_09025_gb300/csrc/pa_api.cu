@@ -37,6 +37,7 @@ struct pa_ctx {
     double icm_lo, icm_hi;
     int* icm_err;               // device flag: a bounded union-find loop gave up
     double* wtab;               // +-J: resampling weight per energy level
+    int* sync;                  // block counters of the merged launches (zeroed)
     int* Rdev;                  // [n_temps] populations in device memory
     std::vector<float> Jh, hh;  // flushed host copies
     // device
@@ -139,15 +140,15 @@ __global__ void acc0_kernel(StepAcc* acc, double betaF0, int R, int* Rdev)
 
 // ---------------- workspace layout ----------------
 
-struct Layout {
-    size_t off[32];
-    size_t total;
-};
-
 enum {
     W_J, W_H, W_JNEG, W_JFIX, W_HFIX, W_BETAS, W_S0, W_S1, W_E32, W_E128, W_PARENT, W_FAM0, W_FAM1,
     W_COUNTS, W_BLOCKSUM, W_W, W_P, W_TOT, W_T, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
-    W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_WTAB, W_COUNT
+    W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_WTAB, W_SYNC, W_COUNT
+};
+
+struct Layout {
+    size_t off[W_COUNT];  // byte offset of every buffer in the workspace
+    size_t total;
 };
 
 static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps, int acc_grad)
@@ -189,6 +190,7 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
     sz[W_RK] = sizeof(double) * n_temps;
     sz[W_RDEV] = sizeof(int) * n_temps;
     sz[W_ICMERR] = sizeof(int);
+    sz[W_SYNC] = sizeof(int) * 4;
     sz[W_WTAB] = kind == PA_PM1 ? sizeof(double) * (size_t)(D * N / 2 + 1) : 0;
     Layout lay;
     size_t off = 0;
@@ -421,6 +423,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->Rk_d = (double*)at(W_RK);
     c->Rdev = (int*)at(W_RDEV);
     c->icm_err = (int*)at(W_ICMERR);
+    c->sync = (int*)at(W_SYNC);
     c->wtab = kind == PA_PM1 ? (double*)at(W_WTAB) : nullptr;
 
     // couplings: sign masks (+-J), fixed-point copies (real)
@@ -463,6 +466,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
         cudaError_t e = cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * (size_t)R, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(StepAcc) * n_temps, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->icm_err, 0, sizeof(int), c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->sync, 0, sizeof(int) * 4, c->st);
         if (e == cudaSuccess && c->acc_grad) {
             e = cudaMemsetAsync(c->cJ, 0, sizeof(unsigned long long) * (size_t)n_temps * D * N, c->st);
             if (e == cudaSuccess) e = cudaMemsetAsync(c->ch, 0, sizeof(unsigned long long) * (size_t)n_temps * N, c->st);
@@ -581,6 +585,7 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         ra.dbeta = c->betas[k] - c->betas[k - 1];
         ra.log_R = std::log((double)Rprev); ra.betaF0 = c->betaF0; ra.k = k;
         ra.wtab = c->wtab; ra.wtab_n = c->wtab ? c->D * c->N / 2 + 1 : 0;  // E - E_min <= 2 D N
+        ra.sync = c->sync;
         ra.key0 = k0; ra.key1 = k1; ra.c3 = pa::counter3(pa::STREAM_RES, c->tag, c->inst);
         c->famcur ^= 1;
     }
@@ -658,6 +663,7 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
     oa.R = R; oa.kind = c->kind == PA_PM1 ? 0 : 1; oa.E32 = c->E32; oa.E128 = c->E128;
     if (dyn) { oa.Rdev = c->Rdev + k; oa.R = c->R; }
     oa.family = c->fam[c->famcur]; oa.part = c->obspart; oa.cur = c->acc + k;
+    oa.sync = c->sync + 2;
     c->k_next = k + 1;
     pl->cur = c->cur;
     pl->famcur = c->famcur;
@@ -697,7 +703,7 @@ static int enqueue_step(pa_ctx* c)
     if (k > 0) {
         ev = phase_begin(c, PA_PHASE_RESAMPLE);
         PA_CK(c, pa::launch_resample(pl.rs, c->st));
-        c->launches += pl.rs.wtab ? 8 : 7;
+        c->launches += pl.rs.wtab ? 6 : 5;
         phase_end(c, PA_PHASE_RESAMPLE, ev);
     }
     ev = phase_begin(c, PA_PHASE_SWEEP);
@@ -721,7 +727,7 @@ static int enqueue_step(pa_ctx* c)
     phase_end(c, PA_PHASE_SWEEP, ev);
     ev = phase_begin(c, PA_PHASE_OBSERVE);
     PA_CK(c, pa::launch_observe(pl.ob, c->st));
-    c->launches += 2;
+    c->launches += 1;
     phase_end(c, PA_PHASE_OBSERVE, ev);
     return PA_OK;
 }
@@ -1323,11 +1329,13 @@ extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_
             rs[at] = pl.rs;
             rs[at].wtab = nullptr;  // the batched resampling computes every weight
             rs[at].wtab_n = 0;
+            rs[at].sync = nullptr;  // and launches every stage
             std::memset(&sw[at], 0, sizeof sw[at]);
             sw[at].cls = cls;
             sw[at].pk = pl.pk.i;
             sw[at].re = pl.re.i;
             ob[at] = pl.ob;
+            ob[at].sync = nullptr;
             b->after_cur[at] = pl.cur;
             b->after_fam[at] = pl.famcur;
         }

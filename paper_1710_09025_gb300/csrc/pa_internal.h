@@ -141,6 +141,10 @@ struct ResampleArgs {
     double* w;                   // [R] weights
     const double* wtab;          // +-J: weight per level (E - E_min) / 4, or null
     int wtab_n;                  // levels in wtab
+    // two zeroed block counters: with them the last block of the weights
+    // launch sums the chunk offsets and the last block of the block-sum launch
+    // scans the block sums (no separate launches); null: separate launches
+    int* sync;
     double* P;                   // [R] local prefix, then P
     double* tot;                 // [nchunks] chunk sums
     double* T;                   // [nchunks + 1] chunk offsets
@@ -172,6 +176,7 @@ struct ObsArgs {
     const int32_t* family;
     ObsPartial* part;            // [kObsBlocks] scratch
     StepAcc* cur;
+    int* sync;                   // zeroed block counter: the last block combines (or null)
 };
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st);
 cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, cudaStream_t st);

@@ -29,6 +29,24 @@ __device__ __forceinline__ double e_minus_min_to_double(const ResampleArgs& a, i
     return __dmul_rn(i128_to_double(ll2_to_i128(a.E128[i]) - emin), 0x1p-96);
 }
 
+// true in the block that finishes last (every block calls it once); the
+// counter is reset for the next launch.  Writes before the call are visible
+// to the last block (fence before the count).
+__device__ __forceinline__ bool last_block(int* counter)
+{
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int done = atomicAdd(counter, 1);
+        s_last = done == (int)(gridDim.x * gridDim.y) - 1;
+        if (s_last) *counter = 0;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
 // source population: in device memory for the nearest-integer scheme
 __device__ __forceinline__ int rs_src(const ResampleArgs& a) { return a.Rsrc ? *a.Rsrc : a.R; }
 
@@ -38,7 +56,7 @@ __device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int c)
     __shared__ double wsh[kChunk];
     const int i0 = c * kChunk;
     const int n = min(kChunk, rs_src(a) - i0);
-    if (n <= 0) return;  // block-uniform
+    if (n <= 0) return;  // block-uniform: past the source population
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         double w;
         const int lv = a.kind == 0 ? a.E32[i0 + t] - (int)a.prev->emin_lo : 0;
@@ -63,7 +81,12 @@ __device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int c)
     __syncthreads();
     for (int t = threadIdx.x; t < n; t += blockDim.x) a.P[i0 + t] = wsh[t];
 }
-__global__ void __launch_bounds__(256) rs_weights_kernel(ResampleArgs a) { rs_weights_body(a, blockIdx.x); }
+__device__ __forceinline__ void rs_offsets_body(const ResampleArgs& a);
+__global__ void __launch_bounds__(256) rs_weights_kernel(ResampleArgs a)
+{
+    rs_weights_body(a, blockIdx.x);
+    if (a.sync && last_block(a.sync) && threadIdx.x < 32) rs_offsets_body(a);  // chunk offsets
+}
 __global__ void __launch_bounds__(256) rs_weights_batched(const ResampleArgs* tab)
 {
     const ResampleArgs& a = tab[blockIdx.y];
@@ -202,10 +225,12 @@ __device__ __forceinline__ void rs_blocksum_body(const int32_t* counts, int R, i
         if (tid == 0) blocksum[b] = v;
     }
 }
+__device__ __forceinline__ void rs_scan_finish(const ResampleArgs& a);
 __global__ void __launch_bounds__(1024) rs_blocksum_kernel(ResampleArgs a)
 {
     const int R = rs_src(a);
     if ((int)blockIdx.x * kScanBlock < R) rs_blocksum_body(a.counts, R, a.blocksum, blockIdx.x);
+    if (a.sync && last_block(a.sync + 1) && threadIdx.x == 0) rs_scan_finish(a);  // block offsets
 }
 __global__ void __launch_bounds__(1024) rs_blocksum_batched(const ResampleArgs* tab)
 {
@@ -223,9 +248,8 @@ __device__ __forceinline__ int rs_scan_blocks_body(int32_t* blocksum, int nb)
     }
     return acc;
 }
-__global__ void rs_scan_blocks_kernel(ResampleArgs a)
+__device__ __forceinline__ void rs_scan_finish(const ResampleArgs& a)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int R = rs_src(a);
     const int total = rs_scan_blocks_body(a.blocksum, (R + kScanBlock - 1) / kScanBlock);
     if (a.Rdst) {  // the drawn population, copies beyond the capacity dropped
@@ -233,6 +257,10 @@ __global__ void rs_scan_blocks_kernel(ResampleArgs a)
         *a.Rdst = Rn;
         *a.Rdst_d = (double)Rn;
     }
+}
+__global__ void rs_scan_blocks_kernel(ResampleArgs a)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) rs_scan_finish(a);
 }
 __global__ void rs_scan_blocks_batched(const ResampleArgs* tab, int n_inst)
 {
@@ -307,14 +335,14 @@ cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
     const int nb = (a.R + kScanBlock - 1) / kScanBlock;
     if (a.wtab) rs_table_kernel<<<(a.wtab_n + 255) / 256, 256, 0, st>>>(a);
     rs_weights_kernel<<<nchunks, 256, 0, st>>>(a);
-    rs_offsets_kernel<<<1, 32, 0, st>>>(a);
+    if (!a.sync) rs_offsets_kernel<<<1, 32, 0, st>>>(a);
     rs_finalize_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
     if (a.scheme == 1)
         rs_nearest_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
     else
         rs_draws_kernel<<<(a.Rn + 255) / 256, 256, 0, st>>>(a);
     rs_blocksum_kernel<<<nb, 1024, 0, st>>>(a);
-    rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a);
+    if (!a.sync) rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a);
     rs_fill_kernel<<<nb, 1024, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -408,7 +436,12 @@ __device__ __forceinline__ void observe_partial_body(const ObsArgs& a)
         a.part[blockIdx.x] = p;
     }
 }
-__global__ void __launch_bounds__(1024) observe_partial_kernel(ObsArgs a) { observe_partial_body(a); }
+__device__ __forceinline__ void observe_final_body(const ObsArgs& a);
+__global__ void __launch_bounds__(1024) observe_partial_kernel(ObsArgs a)
+{
+    observe_partial_body(a);
+    if (a.sync && last_block(a.sync) && threadIdx.x == 0) observe_final_body(a);  // combine in block order
+}
 __global__ void __launch_bounds__(1024) observe_partial_batched(const ObsArgs* tab)
 {
     observe_partial_body(tab[blockIdx.y]);
@@ -445,7 +478,7 @@ __global__ void observe_final_batched(const ObsArgs* tab, int n_inst)
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st)
 {
     observe_partial_kernel<<<kObsBlocks, 1024, 0, st>>>(a);
-    observe_final_kernel<<<1, 32, 0, st>>>(a);
+    if (!a.sync) observe_final_kernel<<<1, 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
