@@ -1,8 +1,9 @@
 """Checkpoint / resume: a run saved after k steps and resumed in a fresh
 context matches the straight run bit for bit (spins, energies, parents,
 families, observables, beta F, gradient counts), for both layouts, both
-coupling kinds, a dynamic population and nearest-integer resampling, and
-through a CUDA graph; checkpoints of another configuration are refused."""
+coupling kinds, a dynamic population, nearest-integer resampling and
+cluster moves, and through a CUDA graph; checkpoints of another
+configuration are refused."""
 import numpy as np
 import pytest
 
@@ -33,6 +34,8 @@ CASES = [
     dict(D=2, L=6, kind=REAL, R=150, layout=0, opts=dict(accumulate_grad=1)),
     dict(D=3, L=4, kind=PM1, R=300, layout=0, opts=dict(populations=[300, 250, 200, 220, 180, 150, 150, 120])),
     dict(D=3, L=4, kind=REAL, R=120, layout=0, opts=dict(resampling=1)),
+    dict(D=2, L=6, kind=PM1, R=150, layout=0, opts=dict(icm=1)),
+    dict(D=3, L=4, kind=PM1, R=101, layout=2, opts=dict(icm=1, resampling=1)),
 ]
 
 
