@@ -115,7 +115,8 @@ int pa_options_default(pa_options* opt);
  *             that energies are exact fixed-point integers at scale 2^-96)
  *   J         host, D*N floats, J[d*N+i] couples i and i+e_d
  *   h         host, N floats or NULL (PA_REAL only)
- *   R         replicas, 1 <= R <= 2^26
+ *   R         replicas, 1 <= R <= 2^26 (with pa_options.populations or the
+ *             nearest-integer scheme: see pa_options for R, targets and capacity)
  *   betas     host, n_temps doubles, betas[0] == 0, non-decreasing, finite
  *   n_sweeps  Metropolis sweeps per temperature (N_S >= 0)
  *   seed      Philox key
@@ -148,7 +149,8 @@ int pa_anneal(pa_ctx* ctx, int n_steps);
 int pa_current_step(const pa_ctx* ctx);
 int pa_synchronize(pa_ctx* ctx);
 
-/* Observables of a completed step k (synchronises). */
+/* Observables of a completed step k (synchronises); out->R is the population
+ * at beta_k.  PA_EEMPTY if the population had died out by step k. */
 int pa_observables(pa_ctx* ctx, int k, pa_obs* out);
 /* beta F_k for every completed k (host, n_temps doubles; unfinished k -> NaN). */
 int pa_free_energy(pa_ctx* ctx, double* host_betaF);
@@ -156,11 +158,12 @@ int pa_free_energy(pa_ctx* ctx, double* host_betaF);
 /*
  * pa_grad -- backward pass of the free-energy estimate.  For the function
  *   f = sum_k gbar[k] * beta_k F_k
- * returns df/dJ_b = sum_k gbar[k] (-beta_k c_b(k) / R) and
- *         df/dh_i = sum_k gbar[k] (-beta_k m_i(k) / R),
+ * returns df/dJ_b = sum_k gbar[k] (-beta_k c_b(k) / R_k) and
+ *         df/dh_i = sum_k gbar[k] (-beta_k m_i(k) / R_k),
  * with c_b(k) = sum_r S_i S_{i+e_d} and m_i(k) = sum_r S_i the exact integer
  * population sums after the sweeps at beta_k (d(beta F)/dJ = -beta <S_i S_j>,
- * d(beta F)/dh = -beta <S_i>; from Eq. 1 and Z = sum exp(-beta H)).
+ * d(beta F)/dh = -beta <S_i>; from Eq. 1 and Z = sum exp(-beta H)), R_k the
+ * population at beta_k.
  * Needs accumulate_grad; gbar host n_temps doubles (entries for steps not yet
  * run must be 0); dJ host D*N doubles, dh host N doubles (or NULL). FP64,
  * summed over k in increasing order. */
