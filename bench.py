@@ -42,6 +42,11 @@ UNIT = "attempts/ns"
 # per-sweep streaming bytes per attempted flip: one spin read and written per
 # sweep (packed: 1 bit each way; int8: 1 byte each way)
 BYTES_PER_ATTEMPT = {"packed": 0.25, "i8": 2.0}
+# streaming bytes per resampled replica (the replica gather is fused into the
+# sweep): energy read 4 (+-J; 16 for int128), weight write 8, local prefix
+# write 8, prefix finalize read + write 16, copy-count atomic 8, block sums
+# read 4, fill: counts read + clear 8, parent write 4, family read + write 8
+RESAMPLE_BYTES_PER_REPLICA = {0: 68, 1: 80}
 
 
 def _peaks():
@@ -285,6 +290,13 @@ def run_gpu(args, wl_name):
         "phases_ms_per_step": per_step,
         "sweep_attempts_per_ns": attempts_step / (sweep_ms * 1e6),
         "resampled_replicas_per_s": R / (rs_ms * 1e-3) if rs_ms > 0 else None,
+        "resample_roofline": ({"bound": "hbm", "achieved": RESAMPLE_BYTES_PER_REPLICA[kind] * R / (rs_ms * 1e-3) / 1e9,
+                               "peak": peak, "unit": "GB/s",
+                               "frac": RESAMPLE_BYTES_PER_REPLICA[kind] * R / (rs_ms * 1e-3) / 1e9 / peak,
+                               "bytes_per_replica": RESAMPLE_BYTES_PER_REPLICA[kind],
+                               "note": "all resampling launches of a step; latency-bound by the fixed-order "
+                                       "sequential FP64 prefix and the binary-search draws"}
+                              if rs_ms > 0 else None),
         "gpu_launches": int(launches1 - launches0),
         "clocks": clocks,
         "observables_last": {"k": args.warmup + args.steps - 1, "E_mean_per_spin": obs_last["E_mean"] / N,
