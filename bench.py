@@ -136,6 +136,23 @@ def _schedule(betas, n_needed):
     return np.concatenate([betas, np.full(n_needed - len(betas), betas[-1])])
 
 
+def _sweep_profile_record():
+    """The committed ncu record of the sweep kernel, if it was taken on the
+    current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "sweep_packed_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    lines = ""
+    for f in d.get("source_files", []):
+        digest = hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest()
+        lines += f"{digest}  {f}\n"
+    if not lines or d.get("source_sha256") != hashlib.sha256(lines.encode()).hexdigest():
+        return None
+    return d
+
+
 def _sweep_profile_traffic():
     """dram bytes per sweep launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
@@ -264,6 +281,7 @@ def run_gpu(args, wl_name):
     bytes_launch = BYTES_PER_ATTEMPT[w["layout"]] * attempts_step
     achieved = bytes_launch / (sweep_ms * 1e-3) / 1e9
     traffic = _sweep_profile_traffic() if w["layout"] == "packed" else None
+    rec = _sweep_profile_record() if w["layout"] == "packed" else None
     rs_ms = phase_ms["resample"] / max(phase_n["resample"], 1)
     per_step = {k: phase_ms[k] / max(phase_n[k], 1) for k in ("resample", "gather", "sweep", "observe")}
 
@@ -286,7 +304,9 @@ def run_gpu(args, wl_name):
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "note": "per-sweep streaming bytes per attempted flip (spin read + written "
                              "each sweep); the kernel keeps the state in shared memory for all N_S "
-                             "sweeps and is bound by integer ALU issue, not DRAM"},
+                             "sweeps and is bound by integer ALU issue, not DRAM",
+                     # the binding unit, from the committed ncu record of this kernel source
+                     "alu_pipe_of_peak_ncu": rec.get("alu_pipe_of_peak") if rec else None},
         "phases_ms_per_step": per_step,
         "sweep_attempts_per_ns": attempts_step / (sweep_ms * 1e6),
         "resampled_replicas_per_s": R / (rs_ms * 1e-3) if rs_ms > 0 else None,
