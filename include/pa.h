@@ -174,6 +174,19 @@ int pa_grad(pa_ctx* ctx, const double* gbar, double* dJ, double* dh);
  * (N + sum_i S^a_i S^b_i) / 2. */
 int pa_overlap(pa_ctx* a, pa_ctx* b, int64_t* hist);
 
+/* Verifies, on the current device (default stream, synchronises), the guard
+ * band that real-coupling sweeps use to take the Metropolis decision of
+ * Sec. II.B without evaluating the specified spec_expf in most lanes: a hardware
+ * estimate g of exp(-x) brackets the specified threshold thr(x) as
+ * trunc(g 2^32 (1 - 2^-14)) <= thr(x) <= trunc(g 2^32 (1 + 2^-14)) + 1.  Every
+ * positive finite float x is checked (about 2^31 values, a few milliseconds).
+ * violations (may be NULL): floats where the bracket fails (0 expected; real
+ * contexts created on a device with violations take the specified rule in every
+ * lane).  max_rel_dev (may be NULL): largest |g / spec_expf(-x) - 1| over
+ * 0 < x <= 87.  Each context runs the check once per device and process at
+ * creation.  PA_ECUDA on a CUDA error (message from pa_last_error(NULL)). */
+int pa_check_accept_band(int64_t* violations, double* max_rel_dev);
+
 /* Copies of the current state to host memory (synchronise).  R below is the
  * current population: populations[last completed step] for the multinomial
  * scheme, the drawn population for the nearest-integer one (pa_sizes reports

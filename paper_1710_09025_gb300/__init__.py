@@ -85,6 +85,7 @@ def load(path: str | None = None):
             "pa_free_energy": (i32, [vp, vp]),
             "pa_grad": (i32, [vp, vp, vp, vp]),
             "pa_overlap": (i32, [vp, vp, vp]),
+            "pa_check_accept_band": (i32, [P(i64), P(ctypes.c_double)]),
             "pa_get_spins": (i32, [vp, vp]),
             "pa_get_spins_range": (i32, [vp, i32, i32, vp]),
             "pa_get_energies": (i32, [vp, vp]),
@@ -248,6 +249,14 @@ def pa_overlap(a, b) -> np.ndarray:
     hist = np.zeros(N + 1, np.int64)
     _check(load().pa_overlap(a, b, _ptr(hist)), a)
     return hist
+
+
+def pa_check_accept_band():
+    """(violations, max_rel_dev) of the real-coupling acceptance guard band on the current device."""
+    v = ctypes.c_int64(0)
+    d = ctypes.c_double(0.0)
+    _check(load().pa_check_accept_band(ctypes.byref(v), ctypes.byref(d)))
+    return int(v.value), float(d.value)
 
 
 def pa_get_spins(ctx) -> np.ndarray:

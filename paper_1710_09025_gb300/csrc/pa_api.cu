@@ -29,6 +29,7 @@ struct pa_ctx {
     int acc_grad;
     cudaStream_t st;
     int gpb, threads, real_warps;
+    int band;                   // real couplings: acceptance guard band verified on this device
     double betaF0, log_R;
     std::vector<double> betas;
     std::vector<int> Rk;        // population (target) at each temperature; R = capacity
@@ -474,12 +475,27 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // host vectors above go out of scope
         if (e != cudaSuccess) { g_create_err = cudaGetErrorString(e); rc2 = PA_ECUDA; }
     }
+    c->band = (rc2 == PA_OK && kind == PA_REAL) ? pa::accept_band_ok(c->st) : 0;
     if (rc2 != PA_OK) {
         if (c->own_ws) cudaFree(c->ws);
         delete c;
         return rc2;
     }
     *out = c;
+    return PA_OK;
+}
+
+extern "C" int pa_check_accept_band(int64_t* violations, double* max_rel_dev)
+{
+    unsigned long long v = 0;
+    double d = 0.0;
+    cudaError_t e = pa::accept_band_check(nullptr, &v, &d);
+    if (e != cudaSuccess) {
+        pa::set_global_error(cudaGetErrorString(e));
+        return PA_ECUDA;
+    }
+    if (violations) *violations = (int64_t)v;
+    if (max_rel_dev) *max_rel_dev = d;
     return PA_OK;
 }
 
@@ -627,6 +643,7 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
     } else {
         pa::RealStep& st = pl->re.s;
         st.k = k; st.n_sweeps = icm ? h1 : c->n_sweeps; st.beta = (float)beta; st.key0 = k0; st.key1 = k1;
+        st.band = c->band;
         st.hs0 = 2u * (uint32_t)(k * c->n_sweeps);
         pa::RealInst& in = pl->re.i;
         in.Sin = c->S8[c->cur]; in.Sout = c->S8[c->cur ^ 1];
@@ -1197,6 +1214,7 @@ struct pa_batch {
     std::vector<int> after_cur, after_fam;  // [k * n_inst + i]: context state after step k
     int maxR;
     bool has_packed;
+    int band;                      // acceptance guard band verified (real instances)
     int tune_mode;                 // 0 tune, -1 defaults
     bool tuned;
     int blocks, mult, tune_slot;
@@ -1258,7 +1276,7 @@ extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_
     b->tune_mode = (opt && opt->threads < 0) ? -1 : 0;
     b->tuned = b->tune_mode < 0;
     b->blocks = 0; b->mult = 1; b->tune_slot = 0; b->tuned_ms = 0.0; b->launches = 0;
-    b->maxR = 0; b->has_packed = false;
+    b->maxR = 0; b->has_packed = false; b->band = 0;
     // validate every instance and size the workspace
     std::vector<size_t> offs(n_inst);
     size_t total = 0;
@@ -1309,6 +1327,7 @@ extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_
             return rc;
         }
         b->ctx.push_back(c);
+        if (d.kind == PA_REAL) b->band = c->band;  // one verdict per device
     }
     // argument tables for every (temperature, instance)
     const size_t nt = (size_t)n_temps * n_inst;
@@ -1412,6 +1431,7 @@ static void batch_step_params(pa_batch* b, int k, pa::PackedStep* ps, pa::RealSt
     fill_packed_step(ps, b->D, b->betas[k], k, b->n_sweeps, k0, k1);
     rs->k = k; rs->n_sweeps = b->n_sweeps; rs->beta = (float)b->betas[k]; rs->key0 = k0; rs->key1 = k1;
     rs->hs0 = 2u * (uint32_t)(k * b->n_sweeps);
+    rs->band = b->band;
 }
 
 // time every candidate sweep configuration on step k; a sweep with k >= 1

@@ -68,6 +68,7 @@ struct RealStep {
     uint32_t hs0;            // 2 (k N_S + first sweep)
     float beta;
     uint32_t key0, key1;
+    int band;                // 1: the acceptance guard band is verified on this device
 };
 struct RealInst {
     const int8_t* Sin;       // rows of NP bytes (+1/-1)
@@ -91,6 +92,12 @@ struct RealSweepArgs {
 cudaError_t launch_sweep_real(int D, int L, const RealSweepArgs& a, int warps, int grid,
                               cudaStream_t st);
 bool real_supported(int D, int L);
+// verifies the acceptance guard band for every positive finite float
+// (violations: count of x where it fails; max_rel_dev: largest |g/e - 1| for
+// 0 < x <= 87); synchronises st
+cudaError_t accept_band_check(cudaStream_t st, unsigned long long* violations, double* max_rel_dev);
+// the verdict for the current device, checked once per process
+int accept_band_ok(cudaStream_t st);
 cudaError_t launch_init_i8(int8_t* S, int N, int NP, int R, uint32_t k0, uint32_t k1, uint32_t c3,
                            cudaStream_t st);
 cudaError_t launch_overlap_i8(const int8_t* A, const int8_t* B, int N, int NP, int R,

@@ -17,7 +17,83 @@
 // >= 2^-73, accumulated in int128, so the sum does not depend on order.
 #include "pa_sweep_tiles.cuh"
 
+#include <cstring>
+#include <mutex>
+
 namespace pa {
+
+// ---- verification of the acceptance guard band ----
+__device__ unsigned long long g_band_violations;
+__device__ unsigned int g_band_maxdev;  // float bits of the largest relative deviation
+
+// every positive finite float x (bit patterns 1 .. 0x7f7fffff)
+__global__ void __launch_bounds__(256) accept_band_check_kernel()
+{
+    unsigned long long viol = 0;
+    float dev = 0.0f;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t u = 1 + blockIdx.x * blockDim.x + threadIdx.x; u <= 0x7f7fffffu; u += stride) {
+        const float x = __uint_as_float(u);
+        const float e = spec_expf(-x);
+        const unsigned long long thr = (e == 1.0f) ? (1ull << 32) : __float2uint_rz(mul32(e, 4294967296.0f));
+        const AcceptBand bd = accept_band(x);
+        viol += (bd.lo > thr) || ((unsigned long long)bd.hi + 1ull < thr);
+        if (x <= 87.0f && e > 0.0f) {
+            const float g = ex2_approx(mul32(x, -0x1.715476p+0f));
+            const double d = fabs((double)g - (double)e) / (double)e;
+            dev = fmaxf(dev, __double2float_ru(d));
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        viol += __shfl_down_sync(0xffffffffu, viol, off);
+        dev = fmaxf(dev, __shfl_down_sync(0xffffffffu, dev, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (viol) atomicAdd(&g_band_violations, viol);
+        atomicMax(&g_band_maxdev, __float_as_uint(dev));  // non-negative floats order as their bits
+    }
+}
+
+cudaError_t accept_band_check(cudaStream_t st, unsigned long long* violations, double* max_rel_dev)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned long long z = 0;
+    const unsigned int zu = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_band_violations, &z, sizeof z, 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_band_maxdev, &zu, sizeof zu, 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    accept_band_check_kernel<<<sms * 8, 256, 0, st>>>();
+    e = cudaGetLastError();
+    unsigned long long v = 0;
+    unsigned int d = 0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(&v, g_band_violations, sizeof v, 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(&d, g_band_maxdev, sizeof d, 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    float df;
+    std::memcpy(&df, &d, sizeof df);
+    if (violations) *violations = v;
+    if (max_rel_dev) *max_rel_dev = df;
+    return cudaSuccess;
+}
+
+int accept_band_ok(cudaStream_t st)
+{
+    static std::mutex mu;
+    static int verdict[64];  // 0 unknown, 1 verified, 2 failed
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> g(mu);
+    if (verdict[dev] == 0) {
+        unsigned long long v = 1;
+        if (accept_band_check(st, &v, nullptr) != cudaSuccess) return 0;
+        verdict[dev] = v == 0 ? 1 : 2;
+    }
+    return verdict[dev] == 1;
+}
 
 // persistent over the instance's tiles of 32 replicas
 template <int D, int L, int WARPS>

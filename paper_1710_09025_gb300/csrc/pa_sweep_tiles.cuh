@@ -580,6 +580,38 @@ __device__ __forceinline__ void real_flush_grad(const RealInst& in, unsigned cha
         if (gh[t]) atomicAdd(&in.ch[t], (unsigned long long)(long long)gh[t]);
 }
 
+// ---- Metropolis acceptance for real couplings (Sec. II.B) ----
+// The specified rule for x = beta dE: accept iff x <= 0, or e == 1, or
+// r < floor(e 2^32) with e = spec_expf(-x).
+__device__ __forceinline__ bool accept_real_exact(float x, uint32_t r)
+{
+    const float e = spec_expf(fminf(-x, 0.0f));
+    return (x <= 0.0f) || (e == 1.0f) || (r < __float2uint_rz(mul32(e, 4294967296.0f)));
+}
+
+// Guard band around the specified threshold, from the hardware base-2
+// exponential g = 2^(-x log2 e) (ex2.approx.ftz, about 2^-20 from exp(-x)):
+// lo = trunc(g 2^32 (1 - 2^-14)), hi = trunc(g 2^32 (1 + 2^-14)).  A lane with
+// r < lo accepts and a lane with r > hi rejects under the specified rule too,
+// provided lo <= thr(x) and hi + 1 >= thr(x) for the specified threshold
+// thr(x) (2^32 when e == 1, else floor(e 2^32)).  accept_band_check verifies
+// both inequalities on the device for every positive finite float x; lanes
+// with lo <= r <= hi (probability about 2^-13 e) take the specified rule.
+struct AcceptBand {
+    uint32_t lo, hi;
+};
+__device__ __forceinline__ float ex2_approx(float y)
+{
+    float g;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(y));
+    return g;
+}
+__device__ __forceinline__ AcceptBand accept_band(float x)
+{
+    const float g = ex2_approx(mul32(x, -0x1.715476p+0f));
+    return {__float2uint_rz(mul32(g, 0x1.fff8p+31f)), __float2uint_rz(mul32(g, 0x1.0004p+32f))};
+}
+
 // replicas [32 tile, 32 tile + 32) of one instance
 template <int D, int L, int WARPS>
 __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealInst& in, int tile,
@@ -656,14 +688,23 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
                     xs[t] = mul32(s.beta, dE);
                     sis[t] = si;
                 }
-                bool accs[4];
+                // decisions: the guard band settles almost every lane; a lane
+                // inside it (or every lane without a verified band) takes the
+                // specified rule, the same decision either way
+                bool accs[4], und[4];
+                bool any = false;
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    // x <= 0 accepts; else r < floor(e 2^32) with e = exp(-x), and
-                    // e == 1 (thr = 2^32) accepts every r
-                    const float e = spec_expf(fminf(-xs[t], 0.0f));
-                    accs[t] = (xs[t] <= 0.0f) || (e == 1.0f) ||
-                              (rs[t] < __float2uint_rz(mul32(e, 4294967296.0f)));
+                    const AcceptBand bd = accept_band(xs[t]);
+                    const bool up = xs[t] > 0.0f;
+                    accs[t] = !up || rs[t] < bd.lo;
+                    und[t] = up && (!s.band || (rs[t] >= bd.lo && rs[t] <= bd.hi));
+                    any |= und[t];
+                }
+                if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (und[t]) accs[t] = accept_real_exact(xs[t], rs[t]);
                 }
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
