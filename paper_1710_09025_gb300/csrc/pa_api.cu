@@ -517,6 +517,14 @@ extern "C" int pa_create_ws(pa_ctx** out, int D, int L, int kind, const float* J
 
 // Per-temperature parameters of the +-J sweep: Metropolis thresholds of the
 // uphill classes dE = 4c as plane masks, and the Philox round keys.
+static void fill_round_keys(uint32_t* rk, uint32_t k0, uint32_t k1)
+{
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+}
+
 static void fill_packed_step(pa::PackedStep* s, int D, double beta, int k, int n_sweeps,
                              uint32_t k0, uint32_t k1)
 {
@@ -536,10 +544,7 @@ static void fill_packed_step(pa::PackedStep* s, int D, double beta, int k, int n
     if (s->always == 0 && s->und == 2u) s->mode = 1;
     else if (s->always == 0 && s->und == 6u) s->mode = 2;
     else s->mode = 0;
-    for (int r = 0; r < 10; ++r) {
-        s->rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
-        s->rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
-    }
+    fill_round_keys(s->rk, k0, k1);
     // class of an uphill lane by its unsatisfied-bond count n: dE / 4 = D - n
     const int cls_n0 = D, cls_n1 = D - 1, cls_n2 = D - 2;
     for (int b = 0; b < 32; ++b) {
@@ -644,6 +649,7 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         pa::RealStep& st = pl->re.s;
         st.k = k; st.n_sweeps = icm ? h1 : c->n_sweeps; st.beta = (float)beta; st.key0 = k0; st.key1 = k1;
         st.band = c->band;
+        fill_round_keys(st.rk, k0, k1);
         st.hs0 = 2u * (uint32_t)(k * c->n_sweeps);
         pa::RealInst& in = pl->re.i;
         in.Sin = c->S8[c->cur]; in.Sout = c->S8[c->cur ^ 1];
@@ -1432,6 +1438,7 @@ static void batch_step_params(pa_batch* b, int k, pa::PackedStep* ps, pa::RealSt
     rs->k = k; rs->n_sweeps = b->n_sweeps; rs->beta = (float)b->betas[k]; rs->key0 = k0; rs->key1 = k1;
     rs->hs0 = 2u * (uint32_t)(k * b->n_sweeps);
     rs->band = b->band;
+    fill_round_keys(rs->rk, k0, k1);
 }
 
 // time every candidate sweep configuration on step k; a sweep with k >= 1

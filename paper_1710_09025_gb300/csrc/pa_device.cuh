@@ -41,14 +41,10 @@ struct u32x4 {
 
 PA_HD void mulhilo(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo)
 {
-#ifdef __CUDA_ARCH__
-    lo = a * b;
-    hi = __umulhi(a, b);
-#else
-    uint64_t p = (uint64_t)a * (uint64_t)b;
+    // one wide multiply gives both halves
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
     lo = (uint32_t)p;
     hi = (uint32_t)(p >> 32);
-#endif
 }
 
 PA_HD u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1)

@@ -69,6 +69,7 @@ struct RealStep {
     float beta;
     uint32_t key0, key1;
     int band;                // 1: the acceptance guard band is verified on this device
+    uint32_t rk[20];         // Philox round keys of (key0, key1), as in PackedStep
 };
 struct RealInst {
     const int8_t* Sin;       // rows of NP bytes (+1/-1)

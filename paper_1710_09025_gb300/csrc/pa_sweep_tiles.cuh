@@ -659,7 +659,7 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
             const int8_t* oth = T + (p ^ 1) * NH * 32;
             int8_t* cur = T + p * NH * 32;
             for (int blk = warp; blk < NB; blk += WARPS) {
-                const u32x4 o = philox((uint32_t)blk, hsw, (uint32_t)r, c3, s.key0, s.key1);
+                const u32x4 o = philox_rk((uint32_t)blk, hsw, (uint32_t)r, c3, s.rk);
                 const uint32_t rs[4] = {o.x, o.y, o.z, o.w};
                 // the four sites of one random-number block are independent (same
                 // parity): fields and energy changes first, then decisions, then stores
