@@ -156,19 +156,8 @@ def _sweep_profile_record():
 def _sweep_profile_traffic():
     """dram bytes per sweep launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "sweep_packed_traffic.json")
-    try:
-        d = json.load(open(p))
-    except Exception:
-        return None
-    # the hash of the kernel's sources at capture time (sha256 of the files' sha256 lines)
-    lines = ""
-    for f in d.get("source_files", []):
-        digest = hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest()
-        lines += f"{digest}  {f}\n"
-    if not lines or d.get("source_sha256") != hashlib.sha256(lines.encode()).hexdigest():
-        return None
-    return d.get("dram_bytes_per_full_launch")
+    rec = _sweep_profile_record()
+    return rec.get("dram_bytes_per_full_launch") if rec else None
 
 
 def oracle_rate(D, L, J, R_sample, betas, n_sweeps, seed, steps=None, kind=0, h=None):
