@@ -82,7 +82,7 @@ typedef struct {
      * Kernels then read the population from device memory, so one CUDA graph
      * serves any population sequence. */
     int32_t capacity;
-    /* isoenergetic cluster moves (Sec. III.C), zero field only: at steps k >= 1
+    /* isoenergetic cluster moves (Sec. II.C), zero field only: at steps k >= 1
      * with icm_beta_lo <= beta_k <= icm_beta_hi (icm_beta_hi <= 0: every step),
      * N_S/2 sweeps, then two rounds of moves on disjoint random pairs (R moves),
      * then the remaining sweeps */

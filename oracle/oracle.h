@@ -82,7 +82,7 @@ or_sim* or_create_ex(int D, int L, int kind, const float* J, const float* h, int
                      const double* betas, int n_temps, int n_sweeps, uint64_t seed,
                      uint32_t rng_instance, uint32_t rng_tag, int accumulate_grad,
                      const int32_t* populations, int scheme, int capacity);
-/* isoenergetic cluster moves (Sec. III.C): at steps k >= 1 with
+/* isoenergetic cluster moves (Sec. II.C): at steps k >= 1 with
  * icm_beta_lo <= beta_k <= icm_beta_hi (hi <= 0: every such step), N_S/2
  * sweeps, two rounds of ICM updates on disjoint random pairs (R updates),
  * then the remaining sweeps.  Needs a zero field. */

@@ -218,7 +218,7 @@ def resample_nearest(kind, E_pairs, beta_prev, beta_next, k, seed, target, cap, 
 
 
 def icm_perm(i, n, k, t, seed, inst=0, tag=0):
-    """pi_t(i): the random pairing permutation of [0, n) (Sec. III.C)."""
+    """pi_t(i): the random pairing permutation of [0, n) (Sec. II.C)."""
     return lib().or_icm_perm(int(i), int(n), int(k), int(t), int(seed), int(inst), int(tag))
 
 

@@ -48,7 +48,7 @@ struct or_sim {
     int D, L, N, kind, R, G, n_temps, n_sweeps, k_next, acc_grad;
     int Rcap, R_src_last;      /* capacity; source population of the last resampling */
     int scheme, dead;          /* resampling scheme; population died out */
-    int icm;                   /* isoenergetic cluster moves (Sec. III.C) */
+    int icm;                   /* isoenergetic cluster moves (Sec. II.C) */
     double icm_lo, icm_hi;     /* beta window of the cluster moves */
     int32_t* Rk;               /* population at each temperature (Sec. III.D, Eq. 6) */
     uint64_t seed;
@@ -250,7 +250,7 @@ static void sweeps(const lat_ctx* c, int kind, int8_t* s, int r0, int nrep, doub
         }
 }
 
-/* ---------------- isoenergetic cluster moves (Sec. III.C) ----------------
+/* ---------------- isoenergetic cluster moves (Sec. II.C) ----------------
  *
  * Two replicas a, b: the overlap q_i = S^a_i S^b_i splits the lattice into
  * islands (connected sets of sites of equal q).  One island is drawn from

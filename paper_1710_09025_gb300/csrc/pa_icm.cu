@@ -1,4 +1,4 @@
-// pa_icm.cu -- isoenergetic cluster moves (Sec. III.C) between random pairs.
+// pa_icm.cu -- isoenergetic cluster moves (Sec. II.C) between random pairs.
 //
 // Round t of step k pairs replicas pi_t(2i) and pi_t(2i+1), i < floor(R/2);
 // pi_t is a 4-round Feistel permutation of [0, 2^m) (m even, the smallest

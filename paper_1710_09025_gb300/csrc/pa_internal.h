@@ -118,7 +118,7 @@ cudaError_t launch_sweep_batched(const PackedStep& ps, const RealStep& rs, const
                                  const int2* items, int n_items, int mult, int* counter, int blocks,
                                  size_t smem, cudaStream_t st);
 
-// ---------------- isoenergetic cluster moves (Sec. III.C) ----------------
+// ---------------- isoenergetic cluster moves (Sec. II.C) ----------------
 struct IcmArgs {
     int D, L, N, NP;
     uint64_t* S;             // packed words [G][N] (or null)

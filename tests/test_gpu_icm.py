@@ -1,4 +1,4 @@
-"""Isoenergetic cluster moves (Sec. III.C) on the GPU against the oracle:
+"""Isoenergetic cluster moves (Sec. II.C) on the GPU against the oracle:
 N_S/2 sweeps, two rounds of moves on disjoint random pairs, the remaining
 sweeps.  Spins, energies, parents, families bit-exact at every step; both
 layouts, both coupling kinds (zero field), odd R and N_S, a beta window,

@@ -1,4 +1,4 @@
-"""Oracle pins for the isoenergetic cluster moves (Sec. III.C): the random
+"""Oracle pins for the isoenergetic cluster moves (Sec. II.C): the random
 pairing is a permutation, one move flips exactly one island of the minority
 overlap sector in both replicas and conserves E_a + E_b, the move leaves the
 Boltzmann distribution invariant (independent exact samples, chi-square),
