@@ -88,6 +88,11 @@ typedef struct {
      * then the remaining sweeps */
     int32_t icm;
     double icm_beta_lo, icm_beta_hi;
+    /* real couplings: 1 takes the specified Metropolis rule (spec_expf
+     * threshold, Sec. II.B) in every lane instead of the verified guard band
+     * of pa_check_accept_band; the decisions, and so every result, are the
+     * same (0: the band where it is verified on the device) */
+    int32_t exact_accept;
 } pa_options;
 
 /* Per-temperature observables (Sec. II.B, Eq. 2-3; Sec. V.A, Eq. 9). */

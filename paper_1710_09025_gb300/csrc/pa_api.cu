@@ -475,7 +475,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // host vectors above go out of scope
         if (e != cudaSuccess) { g_create_err = cudaGetErrorString(e); rc2 = PA_ECUDA; }
     }
-    c->band = (rc2 == PA_OK && kind == PA_REAL) ? pa::accept_band_ok(c->st) : 0;
+    c->band = (rc2 == PA_OK && kind == PA_REAL && !o.exact_accept) ? pa::accept_band_ok(c->st) : 0;
     if (rc2 != PA_OK) {
         if (c->own_ws) cudaFree(c->ws);
         delete c;
@@ -1323,6 +1323,7 @@ extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_
         pa_options o;
         pa_options_default(&o);
         o.rng_instance = d.rng_instance;
+        o.exact_accept = opt ? opt->exact_accept : 0;
         pa_ctx* c = nullptr;
         size_t sz = make_layout(D, d.L, d.kind, resolve_layout(d.kind, &o), d.R, n_temps, 0).total;
         int rc = create_impl(&c, D, d.L, d.kind, d.J, d.h, d.R, betas, n_temps, n_sweeps, seed, &o, stream,
