@@ -25,6 +25,7 @@
 // dE = 2 S_i f (exact), x = f32(beta) dE; accept iff x <= 0 or
 // r < floor(spec_expf(-x) 2^32).  Energies are exact int128 sums of J * 2^96.
 #pragma once
+#include <type_traits>
 #include "pa_device.cuh"
 #include "pa_internal.h"
 
@@ -94,8 +95,8 @@ struct PackedShape {
     static constexpr size_t TILE = (size_t)GPB * 2 * NH * 8;
     static constexpr size_t SJ = ((size_t)N + 15) / 16 * 16;
     static constexpr size_t CNT = (size_t)GPB * NSEG * B * 8;
-    static constexpr int QIPT = 4;  // mode-1 items per thread per queue round
-    static constexpr size_t QUEUE = 32 + (size_t)QIPT * THREADS * (8 + 4);  // mode-1 queue of undecided words
+    static constexpr int QIPT = 4;  // items per thread per queue round
+    static constexpr size_t QUEUE = 32 + (size_t)QIPT * THREADS * (8 + 4);  // queue of undecided words
     static constexpr size_t SMEM = TILE + SJ + CNT + QUEUE;
     static_assert(THREADS % GPB == 0 && (TPG & (TPG - 1)) == 0, "threads per group");
 };
@@ -209,7 +210,8 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     // item t = (group gl, sublattice index q) of parity p: neighbour decoding,
     // unsatisfied-bond counts n = b0 + 2 b1 + 4 b2 per lane, lanes with dE <= 0
     auto classify = [&](int t, int p, const typename LT::Nb& nb_fixed, uint64_t*& cur, int& q,
-                        uint64_t& sw0, uint64_t& b0, uint64_t& b1, uint64_t& b2, uint64_t& down) {
+                        uint64_t& sw0, uint64_t& b0, uint64_t& b1, uint64_t& b2, uint64_t& down,
+                        auto GEN) {
         const int gl = t / NH;
         q = t - gl * NH;
         cur = sm + (gl * 2 + p) * NH;
@@ -218,7 +220,9 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
         // when every item of this thread sits on the same sublattice site
         // (THREADS a multiple of N/2) decode once; when it sits on the same x-y
         // column (3D, THREADS a multiple of L^2/2) only z moves
-        if constexpr (THREADS % NH == 0) {
+        if constexpr (decltype(GEN)::value) {
+            nb = LT::neighbours(p, q);
+        } else if constexpr (THREADS % NH == 0) {
             nb = nb_fixed;
         } else if constexpr (D == 3 && THREADS % (LT::LH * L) == 0) {
             nb = LT::neighbours_column(p, q, xh_c, y_c);
@@ -268,15 +272,16 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                                (D == 3) ? s.v10[2 * m + 1] : s.v01[2 * m + 1], U, acc);
         }
     };
-    auto compare_mode02 = [&](uint32_t q, uint32_t g, uint32_t hs, uint64_t U, uint64_t b0, uint64_t b1,
-                              uint64_t& acc) {
+    auto compare_mode02 = [&](uint32_t q, uint32_t g, uint32_t hs, uint64_t& U, uint64_t b0, uint64_t b1,
+                              uint64_t& acc, auto M0, auto M1) {
+        constexpr int m0 = decltype(M0)::value, m1 = decltype(M1)::value;
         // planes where every threshold bit is 0 only reject (a 1 in r decides
         // r > thr): one masking step instead of the class selection
         const uint32_t zp = s.zero_planes;
         if (s.mode == 2) {
             const uint64_t sel = (D == 3) ? b1 : b0;  // 1 selects the dE = 4 class
 #pragma unroll
-            for (int m = 0; m < 16; ++m) {
+            for (int m = m0; m < m1; ++m) {
                 if (!U) break;
                 const u32x4 o = philox_rk(q, hs, 16u * g + (uint32_t)m, c3, s.rk);
                 const uint64_t p0 = (uint64_t)o.x | ((uint64_t)o.y << 32);
@@ -291,7 +296,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
         } else if ((zp & 3u) == 3u) {
             // thresholds below 2^30: leading planes only reject
 #pragma unroll
-            for (int m = 0; m < 16; ++m) {
+            for (int m = m0; m < m1; ++m) {
                 if (!U) break;
                 const u32x4 o = philox_rk(q, hs, 16u * g + (uint32_t)m, c3, s.rk);
                 const uint64_t p0 = (uint64_t)o.x | ((uint64_t)o.y << 32);
@@ -304,7 +309,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
         } else {
             // high temperature: threshold bits of 1 from the first planes on
 #pragma unroll
-            for (int m = 0; m < 16; ++m) {
+            for (int m = m0; m < m1; ++m) {
                 if (!U) break;
                 const u32x4 o = philox_rk(q, hs, 16u * g + (uint32_t)m, c3, s.rk);
                 plane_step((uint64_t)o.x | ((uint64_t)o.y << 32), s.v00[2 * m], s.v01[2 * m],
@@ -334,7 +339,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
             U = (m1 & und1) | (m2 & und2) | (m3 & und3);
         }
     };
-    // mode-1 queue: per round two counters (entries, next entry to take), then
+    // block queue: per round two counters (entries, next entry to take), then
     // the undecided masks and item indices
     int* qn = reinterpret_cast<int*>(qbuf);
     uint64_t* QU = reinterpret_cast<uint64_t*>(qbuf + 32);
@@ -342,9 +347,14 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     if (tid < 4) qn[tid] = 0;
     __syncthreads();
     int round = 0;
-    // compaction pays only in mode 1 (measured at L=16: mode 1 steps 14.5 ->
-    // 12.0 ms; modes 2 and 0, where most words have undecided lanes, get slower)
+    // mode 1 compacts every word with undecided lanes (at low temperature
+    // most words have none: L=16 mode-1 steps 14.5 -> 12.0 ms); modes 0 and 2,
+    // where most words have undecided lanes, compact only the words still
+    // undecided after the first calls (below)
     const bool compact = s.mode == 1;
+    // late compaction is measured faster on the 3D L=16 tile only (smaller
+    // tiles, as in the disorder batch, pay more for the extra queue round)
+    constexpr bool kLate = D == 3 && L >= 16;
 
     for (int sw = 0; sw < s.n_sweeps; ++sw) {
         for (int p = 0; p < 2; ++p) {
@@ -367,7 +377,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                             uint64_t* cur;
                             int q;
                             uint64_t sw0, b0, b1, b2, down;
-                            classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
+                            classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down, std::false_type{});
                             cur[q] = sw0 ^ down;  // no uphill class is always accepted in mode 1
                             U = ~down & ((D == 3) ? b1 : b0);
                         }
@@ -392,17 +402,68 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     }
                     __syncthreads();
                 }
-            } else {
+            } else if constexpr (!kLate) {
                 for (int t = tid; t < ng * NH; t += THREADS) {
                     uint64_t* cur;
                     int q;
                     uint64_t sw0, b0, b1, b2, down, acc, U;
-                    classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
+                    classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down, std::false_type{});
                     start(b0, b1, b2, down, acc, U);
-                    compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc);
+                    compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
+                                   std::integral_constant<int, 0>{}, std::integral_constant<int, 16>{});
                     cur[q] = sw0 ^ acc;
                 }
                 __syncthreads();
+            } else {
+                // Late compaction: every word gets its first KLATE Philox calls
+                // (8 planes) in place; a warp then waits for its slowest word only
+                // that far.  The ~12 % of words still undecided go to the block
+                // queue and finish there on full warps.  Same counters, so the
+                // same decisions (L=16: 3927 -> 3817 ms of sweeps per schedule;
+                // 3 calls: 4083 ms, 5 calls: 3937 ms)
+                constexpr int KLATE = 4;
+                for (int base = 0; base < ng * NH; base += SH::QIPT * THREADS, ++round) {
+                    int* cnt_r = qn + 2 * (round & 1);
+#pragma unroll
+                    for (int it = 0; it < SH::QIPT; ++it) {
+                        const int t = base + it * THREADS + tid;
+                        uint64_t U = 0;
+                        if (t < ng * NH) {
+                            uint64_t* cur;
+                            int q;
+                            uint64_t sw0, b0, b1, b2, down, acc;
+                            classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down, std::false_type{});
+                            start(b0, b1, b2, down, acc, U);
+                            compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
+                                           std::integral_constant<int, 0>{}, std::integral_constant<int, KLATE>{});
+                            cur[q] = sw0 ^ acc;
+                        }
+                        const unsigned bal = __ballot_sync(0xffffffffu, U != 0);
+                        int wb = 0;
+                        if (lane == 0 && bal) wb = atomicAdd(cnt_r, __popc(bal));
+                        wb = __shfl_sync(0xffffffffu, wb, 0);
+                        if (U) {
+                            const int slot = wb + __popc(bal & ((1u << lane) - 1u));
+                            QU[slot] = U;
+                            Qt[slot] = t;
+                        }
+                    }
+                    __syncthreads();
+                    const int n = cnt_r[0];
+                    if (tid == 0) { qn[2 * ((round + 1) & 1)] = 0; qn[2 * ((round + 1) & 1) + 1] = 0; }
+                    for (int e = atomicAdd(cnt_r + 1, 1); e < n; e = atomicAdd(cnt_r + 1, 1)) {
+                        const int t2 = Qt[e];
+                        uint64_t* cur2;
+                        int q2;
+                        uint64_t sw1, b0, b1, b2, down, acc2 = 0, U2 = QU[e];
+                        // lanes still undecided were not flipped: their counts are unchanged
+                        classify(t2, p, nb_fixed, cur2, q2, sw1, b0, b1, b2, down, std::true_type{});
+                        compare_mode02((uint32_t)q2, (uint32_t)(g0 + t2 / NH), hs, U2, b0, b1, acc2,
+                                       std::integral_constant<int, KLATE>{}, std::integral_constant<int, 16>{});
+                        cur2[q2] = sw1 ^ acc2;
+                    }
+                    __syncthreads();
+                }
             }
         }
     }
