@@ -14,7 +14,9 @@
 // stored as 32 bit planes (plane b holds bit 31-b of the 64 lanes' r), so
 // r < thr is decided MSB first at the first plane where a lane's bit differs
 // from thr's; planes are generated two at a time only while undecided lanes
-// remain (same decisions as generating all 32).  Energies: per-lane counts of
+// remain (same decisions as generating all 32).  Words still undecided after
+// the first calls (mode 1: any; modes 0 and 2 at L=16: after four calls) are
+// compacted into a block queue and finished on full warps.  Energies: per-lane counts of
 // unsatisfied bonds in bit-sliced counters, reduced across the threads of a
 // group with warp shuffles; E = 2 n_unsat - D N.
 //
@@ -23,7 +25,9 @@
 // replicas; couplings are warp-uniform broadcast loads.  Local field
 // f = ((((t_-x + t_+x) + t_-y) + t_+y) + ...) + h_i in FP32 with t = J S_nb,
 // dE = 2 S_i f (exact), x = f32(beta) dE; accept iff x <= 0 or
-// r < floor(spec_expf(-x) 2^32).  Energies are exact int128 sums of J * 2^96.
+// r < floor(spec_expf(-x) 2^32), decided through a device-verified guard band
+// around that threshold (same decisions; see accept_band).  Energies are
+// exact int128 sums of J * 2^96.
 #pragma once
 #include <type_traits>
 #include "pa_device.cuh"
