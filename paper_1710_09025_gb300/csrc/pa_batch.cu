@@ -37,11 +37,11 @@ __global__ void __launch_bounds__(kBatchThreads, 3) sweep_batch_kernel(PackedSte
 #define XP(idx, l)                                                                                  \
     case 2 * idx: {                                                                                 \
         constexpr int g = default_shape<3, l>().gpb;                                                \
-        sweep_packed_tile<3, l, g, kBatchThreads, false>(ps, bi.pk, w.y * g, smem_b);               \
+        sweep_packed_tile<3, l, g, kBatchThreads, false, false>(ps, bi.pk, w.y * g, smem_b);               \
     } break;                                                                                        \
     case 2 * idx + 1: {                                                                             \
         constexpr int g = 2 * default_shape<3, l>().gpb;                                            \
-        sweep_packed_tile<3, l, g, kBatchThreads, false>(ps, bi.pk, w.y * g, smem_b);               \
+        sweep_packed_tile<3, l, g, kBatchThreads, false, false>(ps, bi.pk, w.y * g, smem_b);               \
     } break;
             PA_BATCH_PACKED(XP)
 #undef XP

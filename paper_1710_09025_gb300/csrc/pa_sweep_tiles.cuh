@@ -122,7 +122,9 @@ template <int D, int L> __host__ __device__ constexpr Shape default_shape()
 }
 
 // groups [g0, g0 + GPB) of one instance; smem holds PackedShape::SMEM bytes
-template <int D, int L, int GPB, int THREADS, bool I8>
+// LATE: allow the late compaction of modes 0 and 2 (the single-instance
+// kernels; the disorder batch measured slower with it)
+template <int D, int L, int GPB, int THREADS, bool I8, bool LATE = true>
 __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const PackedInst& in, int g0,
                                                   unsigned char* smem)
 {
@@ -356,9 +358,10 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     // where most words have undecided lanes, compact only the words still
     // undecided after the first calls (below)
     const bool compact = s.mode == 1;
-    // late compaction is measured faster on the 3D L=16 tile only (smaller
-    // tiles, as in the disorder batch, pay more for the extra queue round)
-    constexpr bool kLate = D == 3 && L >= 16;
+    // late compaction is measured faster for single 3D instances with L >= 8
+    // (L=8: 2182 -> 2273 attempts/ns; L=16: 3108 -> 3197); the disorder batch
+    // (L = 4..10, doubled groups per block) measured slower and keeps the loop
+    constexpr bool kLate = LATE && D == 3 && L >= 8;
 
     for (int sw = 0; sw < s.n_sweeps; ++sw) {
         for (int p = 0; p < 2; ++p) {
