@@ -21,48 +21,11 @@
 // Energies: per-lane unsatisfied-bond counts are accumulated in bit-sliced
 // (vertical) counters, reduced across the threads of a group with warp
 // shuffles, and E = 2 n_unsat - D N.
-#include "pa_sweep_tiles.cuh"
+#include "pa_packed_sweep.cuh"
 
 namespace pa {
 
-template <int D, int L, int GPB, int THREADS, bool I8>
-__global__ void __launch_bounds__(THREADS, 4) sweep_packed_kernel(PackedSweepArgs a)
-{
-    extern __shared__ __align__(16) unsigned char smem_packed[];
-    sweep_packed_tile<D, L, GPB, THREADS, I8>(a.s, a.i, blockIdx.x * GPB, smem_packed);
-}
-
 // ---------------- shapes and dispatch ----------------
-
-template <int D, int L, int GPB, int THREADS, bool I8>
-static cudaError_t launch_one(const PackedSweepArgs& a, cudaStream_t st)
-{
-    const size_t smem = PackedShape<D, L, GPB, THREADS>::SMEM;
-    auto kern = sweep_packed_kernel<D, L, GPB, THREADS, I8>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
-    int grid = (a.i.G + GPB - 1) / GPB;
-    kern<<<grid, THREADS, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int D, int L>
-static cudaError_t launch_dl(const PackedSweepArgs& a, int gpb, int threads, cudaStream_t st)
-{
-    constexpr Shape s = default_shape<D, L>();
-    const bool i8 = a.i.S8_out != nullptr;
-    // the one tuned alternative: twice the groups per block, same thread count
-    if (gpb == 2 * s.gpb && threads == s.threads)
-        return i8 ? launch_one<D, L, 2 * s.gpb, s.threads, true>(a, st)
-                  : launch_one<D, L, 2 * s.gpb, s.threads, false>(a, st);
-    if (gpb != s.gpb || threads != s.threads) return cudaErrorInvalidConfiguration;
-    return i8 ? launch_one<D, L, s.gpb, s.threads, true>(a, st)
-              : launch_one<D, L, s.gpb, s.threads, false>(a, st);
-}
 
 #define PA_PACKED_CASES(X) \
     X(3, 2) X(3, 4) X(3, 6) X(3, 8) X(3, 10) X(3, 12) X(3, 16) \
@@ -87,10 +50,12 @@ void packed_default_shape(int D, int L, int* gpb, int* threads)
 cudaError_t launch_sweep_packed(int D, int L, const PackedSweepArgs& a, int gpb, int threads,
                                 cudaStream_t st)
 {
-#define X(d, l) if (D == d && L == l) return launch_dl<d, l>(a, gpb, threads, st);
-    PA_PACKED_CASES(X)
-#undef X
-    return cudaErrorInvalidValue;
+    bool handled = false;
+    cudaError_t e = launch_sweep_packed_part0(D, L, a, gpb, threads, st, &handled);
+    if (!handled) e = launch_sweep_packed_part1(D, L, a, gpb, threads, st, &handled);
+    if (!handled) e = launch_sweep_packed_part2(D, L, a, gpb, threads, st, &handled);
+    if (!handled) e = launch_sweep_packed_part3(D, L, a, gpb, threads, st, &handled);
+    return handled ? e : cudaErrorInvalidValue;
 }
 
 // ---------------- init, gather, unpack, overlap ----------------
