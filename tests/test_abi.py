@@ -131,3 +131,20 @@ def test_product_never_imports_or_links_the_oracle():
         for f in fs:
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 assert not pat.search(open(os.path.join(dp, f)).read()), f
+
+
+def test_packed_sweep_parts_cover_every_lattice_once():
+    """The packed sweep's lattice sizes are instantiated in four translation
+    units; together they must list every supported (D, L) exactly once."""
+    import re
+    csrc = os.path.join(ROOT, "paper_1710_09025_gb300", "csrc")
+    main = open(os.path.join(csrc, "pa_packed.cu")).read()
+    block = main[main.index("#define PA_PACKED_CASES(X)"):main.index("bool packed_supported")]
+    supported = re.findall(r"X\((\d), (\d+)\)", block)
+    parts = []
+    for k in range(4):
+        src = open(os.path.join(csrc, f"pa_packed_part{k}.cu")).read()
+        body = src[src.index("#define X(d, l)"):src.index("#undef X")]
+        parts += re.findall(r"X\((\d), (\d+)\)", body.split("\n", 1)[1])
+    assert len(parts) == len(set(parts))
+    assert sorted(parts) == sorted(supported) and len(supported) == 16
