@@ -7,7 +7,9 @@ computed independently of the oracle:
   * <E> and beta F_k = -ln Z(beta_k) of the anneal against numpy enumeration
     of the 4 x 4 torus (+-J without field; Gaussian couplings with a field),
     z-tests over eight seeds (Sec. II.A, Eq. 1; Sec. II.B);
-  * the energies the run reports against a numpy recompute from its spins.
+  * the energies the run reports against a numpy recompute from its spins;
+  * multinomial resampling on fixed energies: copy numbers against numpy
+    weights (chi-square) and ln Q against its numpy value.
 The unmodified oracle passes the same pins; every mutant fails at least one.
 The committed oracle is never modified.
 """
@@ -46,6 +48,11 @@ MUTANTS = [
      "*lnQ = (-(db * e_to_double(kind, emin)) + log(S));"),
     ("beta F sign", "pamc.c",
      "o[4] = -(double)s->N * log(2.0) - s->sum_lnQ;", "o[4] = -(double)s->N * log(2.0) + s->sum_lnQ;"),
+    ("draw lands on the next replica", "pamc.c",
+     "counts[lo] += 1;", "counts[lo + 1 < R ? lo + 1 : lo] += 1;"),
+    ("weight exponent sign", "pamc.c",
+     "w[r] = or_spec_exp64(-(db * e_to_double(kind, E[r] - emin)));",
+     "w[r] = or_spec_exp64(-(db * e_to_double(kind, emin - E[r])));"),
 ]
 
 
@@ -90,8 +97,35 @@ def _load(path):
     return mod
 
 
-def _failed_pins(O):
+def _failed_resampling_pins(O):
+    """Multinomial resampling on fixed energies (Sec. II.B): copy numbers sum
+    to R, their means follow R w_i / S with w_i from numpy (chi-square over
+    100 draws of the population), and ln Q = -dbeta E_min + ln S - ln R."""
     fails = []
+    rng = np.random.default_rng(42)
+    R = 400
+    E = rng.integers(-40, 0, R) * 4
+    pairs = np.stack([E, -np.ones(R, np.int64)], 1).reshape(-1)
+    w = np.exp(-0.05 * (E - E.min()))
+    tot = np.zeros(R)
+    M = 100
+    for k in range(1, M + 1):
+        r = O.resample(PM1, pairs, 1.0, 1.05, k, seed=9)
+        if r["counts"].sum() != R:
+            return ["resampling: population"]
+        tot += r["counts"]
+    expct = M * R * w / w.sum()
+    chi2 = ((tot - expct) ** 2 / expct).sum()
+    if not abs(chi2 - (R - 1)) < 6 * math.sqrt(2 * (R - 1)):
+        fails.append("resampling: copy numbers")
+    lnQ = -0.05 * E.min() + math.log(w.sum()) - math.log(R)
+    if not abs(r["lnQ"] - lnQ) < 1e-10 * abs(lnQ):
+        fails.append("resampling: ln Q")
+    return fails
+
+
+def _failed_pins(O):
+    fails = _failed_resampling_pins(O)
     cases = [("pm", PM1, W.couplings_pm(D, L, 61).astype(np.float32), None),
              ("gauss+h", REAL, W.couplings_gauss(D, L, 62), W.field_uniform(N, 63))]
     for name, kind, J, h in cases:
