@@ -268,14 +268,18 @@ void pa_batch_destroy(pa_batch* b);
 
 /*
  * pa_resample_static -- the resampling step of pa_anneal_step for a +-J
- * population, for callers that cannot allocate device memory (code inside a
- * CUDA graph being captured, allocator-less embedded runtimes, hosts whose
- * memory manager owns every device byte).  The paper has no counterpart; it
- * exists for those callers.  No cudaMalloc, cudaFree or allocating library
- * call is made: the scratch (weights, prefix sums, copy numbers, families)
- * lives in one file-scope device array of PA_STATIC_SCRATCH_BYTES, which every
- * GPU that loads the library keeps until the process exits.
- *   d_E        device, R int32 energies of the population at beta_prev
+ * population, for callers that cannot allocate device memory: allocator-less
+ * embedded runtimes, and hosts whose memory manager owns every device byte and
+ * hands the library only its input and output buffers.  The paper has no
+ * counterpart; it exists for those callers.  No cudaMalloc, cudaFree or
+ * allocating library call is made: the scratch (weights, prefix sums, copy
+ * numbers, families) lives in one file-scope device array of
+ * PA_STATIC_SCRATCH_BYTES, which every GPU that loads the library keeps until
+ * the process exits.
+ *   d_E        device, R int32 energies (+-J only: integer energies of the
+ *              population at beta_prev, i.e. after the sweeps of step k-1);
+ *              E_min is taken as the minimum of d_E (pa_anneal_step takes the
+ *              same minimum from the previous step's observables)
  *   R          1 <= R <= PA_STATIC_MAX_R; larger R returns PA_EINVAL
  *   beta_prev, beta_next   finite, beta_prev <= beta_next
  *   k          temperature index of the step (selects the draw stream)
@@ -283,12 +287,15 @@ void pa_batch_destroy(pa_batch* b);
  *   d_parent   device, R int32 out: slot j takes replica d_parent[j]
  *   d_lnQ      device, 1 double out: ln Q of this step
  *   stream     cudaStream_t (NULL = legacy default stream)
- * Results equal what pa_anneal_step computes for the same energies and step.
- * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (that device must be current); make that first call
- * before any stream capture.  Every call shares the one array and keeps the
- * last call's contents: calls whose kernels overlap on the GPU (two streams,
- * two host threads) race and must be serialised by the caller.
+ * Results are bit-identical to what pa_anneal_step computes for the same
+ * energies and step (parents and ln Q).  The first call on a device looks up
+ * the array's device address with cudaGetSymbolAddress (that device must be
+ * current) and caches it for the life of the process; make that first call
+ * before any stream capture.  A device reset (cudaDeviceReset) after the first
+ * call is not supported: the cached address would be stale.  Every call shares
+ * the one array and keeps the last call's contents (each call clears what it
+ * needs zeroed): calls whose kernels overlap on the GPU (two streams, two host
+ * threads) race and must be serialised by the caller.
  * Errors: PA_EINVAL, PA_ECUDA; message in pa_last_error(NULL).
  */
 #define PA_STATIC_MAX_R 65536

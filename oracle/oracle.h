@@ -133,6 +133,8 @@ int or_resample(int kind, int R, const int64_t* E, double beta_prev, double beta
 void or_energies(int D, int L, int kind, const float* J, const float* h, int R,
                  const int8_t* spins, int64_t* E /* 2R */);
 int  or_overlap(int N, int R, const int8_t* a, const int8_t* b, int64_t* hist /* N+1 */);
+/* sum_r S_i S_{i+e_d} (cJ, D*N) and sum_r S_i (ch, N) of R int8 rows */
+int  or_grad_counts(int D, int L, int R, const int8_t* spins, int64_t* cJ, int64_t* ch);
 
 /* ---- exact enumeration (exact.c), N <= 24 ---- */
 /* out[b*8 + 0..7] = lnZ, E_mean, E2_mean, C, betaF, E_ground, (0), (0) */

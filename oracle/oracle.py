@@ -96,6 +96,7 @@ def lib():
                                       vp, vp]),
                 "or_energies": (None, [i32, i32, i32, vp, vp, i32, vp, vp]),
                 "or_overlap": (i32, [i32, i32, vp, vp, vp]),
+                "or_grad_counts": (i32, [i32, i32, i32, vp, vp, vp]),
                 "or_exact": (i32, [i32, i32, vp, vp, i32, vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
@@ -240,6 +241,18 @@ def overlap(N, a, b):
     hist = np.zeros(N + 1, np.int64)
     lib().or_overlap(N, a.shape[0], _p(a), _p(b), _p(hist))
     return hist
+
+
+def grad_counts(D, L, spins):
+    """(cJ, ch): sum_r S_i S_{i+e_d} per bond d*N+i and sum_r S_i per site of
+    R int8 rows (R x N)."""
+    spins = np.ascontiguousarray(spins, dtype=np.int8)
+    N = L ** D
+    cJ = np.zeros(D * N, np.int64)
+    ch = np.zeros(N, np.int64)
+    rc = lib().or_grad_counts(D, L, spins.shape[0], _p(spins), _p(cJ), _p(ch))
+    assert rc == 0
+    return cJ, ch
 
 
 def exact(D, L, J, h, betas, want_corr=False):

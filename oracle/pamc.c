@@ -660,6 +660,22 @@ void or_destroy(or_sim* s)
     free(s);
 }
 
+/* Population sums for the gradient of beta F (from Eq. 1 with the field term
+ * and Z = sum exp(-beta H)): c_b += sum_r S_i S_{i+e_d} for bond b = d N + i,
+ * m_i += sum_r S_i, over R replicas given as int8 rows. */
+static void grad_counts_add(int D, int N, const int32_t* nbr, int R, const int8_t* spins,
+                            int64_t* cJ, int64_t* ch)
+{
+    for (int r = 0; r < R; ++r) {
+        const int8_t* sr = spins + (size_t)r * N;
+        for (int i = 0; i < N; ++i) {
+            ch[i] += sr[i];
+            for (int d = 0; d < D; ++d)
+                cJ[d * N + i] += sr[i] * sr[nbr[i * 2 * D + 2 * d + 1]];
+        }
+    }
+}
+
 static void measure(or_sim* s, int k, double lnQ)
 {
     lat_ctx c = lat_of(s);
@@ -703,18 +719,9 @@ static void measure(or_sim* s, int k, double lnQ)
     o[5] = Sf;
     o[6] = (double)s->R / exp(Sf);
     o[7] = (double)s->R;
-    if (s->acc_grad) {
-        int64_t* cJ = s->cJ + (size_t)k * s->D * s->N;
-        int64_t* ch = s->ch + (size_t)k * s->N;
-        for (int r = 0; r < s->R; ++r) {
-            const int8_t* sr = s->s + (size_t)r * s->N;
-            for (int i = 0; i < s->N; ++i) {
-                ch[i] += sr[i];
-                for (int d = 0; d < s->D; ++d)
-                    cJ[d * s->N + i] += sr[i] * sr[s->nbr[i * 2 * s->D + 2 * d + 1]];
-            }
-        }
-    }
+    if (s->acc_grad)
+        grad_counts_add(s->D, s->N, s->nbr, s->R, s->s, s->cJ + (size_t)k * s->D * s->N,
+                        s->ch + (size_t)k * s->N);
 }
 
 int or_step(or_sim* s)
@@ -857,5 +864,21 @@ int or_overlap(int N, int R, const int8_t* a, const int8_t* b, int64_t* hist)
         for (int i = 0; i < N; ++i) ndiff += a[(size_t)r * N + i] != b[(size_t)r * N + i];
         hist[N - ndiff] += 1;
     }
+    return 0;
+}
+
+/* Gradient counts of one population given as int8 rows (R x N): cJ (D*N) and
+ * ch (N) are overwritten with sum_r S_i S_{i+e_d} and sum_r S_i. */
+int or_grad_counts(int D, int L, int R, const int8_t* spins, int64_t* cJ, int64_t* ch)
+{
+    int N = ipow(L, D);
+    int32_t* nbr = (int32_t*)malloc(sizeof(int32_t) * (size_t)N * 2 * D);
+    int32_t* bond = (int32_t*)malloc(sizeof(int32_t) * (size_t)N * 2 * D);
+    if (!nbr || !bond) { free(nbr); free(bond); return -1; }
+    or_lattice(D, L, nbr, bond);
+    memset(cJ, 0, sizeof(int64_t) * (size_t)D * N);
+    memset(ch, 0, sizeof(int64_t) * (size_t)N);
+    grad_counts_add(D, N, nbr, R, spins, cJ, ch);
+    free(nbr); free(bond);
     return 0;
 }

@@ -1,9 +1,8 @@
 // pa_noalloc.cu -- resampling without any device allocation.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// graph that is being captured, allocator-less embedded runtimes, or hosts
-// whose memory manager owns every device byte and hands out only the input
-// and output buffers.  pa_resample_static gives them the resampling step of
+// Some callers cannot call cudaMalloc at all: allocator-less embedded
+// runtimes, or hosts whose memory manager owns every device byte and hands
+// out only the input and output buffers.  pa_resample_static gives them the resampling step of
 // pa_anneal_step (weights, fixed-order prefix, multinomial draws, parents,
 // ln Q) with its scratch in one file-scope device array instead of a
 // context workspace.  The caller passes only inputs and outputs.
@@ -12,7 +11,8 @@
 // PA_STATIC_SCRATCH_BYTES until the process exits.  Host code may not pass
 // the array's name to a kernel (on the host it is only a stand-in symbol),
 // so the device address is looked up once per device with
-// cudaGetSymbolAddress while that device is current, and cached.
+// cudaGetSymbolAddress while that device is current, and cached for the life
+// of the process (a device reset after the first call is not supported).
 #include "pa.h"
 #include "pa_device.cuh"
 #include "pa_internal.h"
