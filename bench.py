@@ -386,7 +386,8 @@ def batched_vs_plain(P, args):
                     if not same:
                         break
                 same_all = same_all and same
-                cfg = P.pa_batch_sweep_config(a)
+                if cfg is None:  # the tuned configuration (later batches reuse the cached choice)
+                    cfg = P.pa_batch_sweep_config(a)
             finally:
                 P.pa_batch_destroy(a)
                 P.pa_batch_destroy(b)
