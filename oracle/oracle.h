@@ -133,6 +133,10 @@ int or_resample(int kind, int R, const int64_t* E, double beta_prev, double beta
 void or_energies(int D, int L, int kind, const float* J, const float* h, int R,
                  const int8_t* spins, int64_t* E /* 2R */);
 int  or_overlap(int N, int R, const int8_t* a, const int8_t* b, int64_t* hist /* N+1 */);
+/* cumulative resampling weights P (n) of weights w in the fixed summation
+ * order, and (if prefix_out is not NULL) the prefix sums before the running
+ * maximum */
+void or_weight_prefix(const double* w, int n, double* P_out, double* prefix_out);
 /* sum_r S_i S_{i+e_d} (cJ, D*N) and sum_r S_i (ch, N) of R int8 rows */
 int  or_grad_counts(int D, int L, int R, const int8_t* spins, int64_t* cJ, int64_t* ch);
 

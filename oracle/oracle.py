@@ -97,6 +97,7 @@ def lib():
                 "or_energies": (None, [i32, i32, i32, vp, vp, i32, vp, vp]),
                 "or_overlap": (i32, [i32, i32, vp, vp, vp]),
                 "or_grad_counts": (i32, [i32, i32, i32, vp, vp, vp]),
+                "or_weight_prefix": (None, [vp, i32, vp, vp]),
                 "or_exact": (i32, [i32, i32, vp, vp, i32, vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
@@ -241,6 +242,16 @@ def overlap(N, a, b):
     hist = np.zeros(N + 1, np.int64)
     lib().or_overlap(N, a.shape[0], _p(a), _p(b), _p(hist))
     return hist
+
+
+def weight_prefix(w):
+    """(P, prefix): cumulative resampling weights of w in the fixed summation
+    order (fan-out 32), and the prefix sums before the running maximum."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    P = np.empty(len(w))
+    pre = np.empty(len(w))
+    lib().or_weight_prefix(_p(w), len(w), _p(P), _p(pre))
+    return P, pre
 
 
 def grad_counts(D, L, spins):

@@ -388,7 +388,60 @@ static i128 energy_one(const lat_ctx* c, int kind, const int8_t* sr)
 
 /* ---------------- resampling (Sec. II.B) ---------------- */
 
-#define OR_CHUNK 1024
+/* Fan-out of the fixed summation order of the resampling weights. */
+#define OR_FANOUT 32
+
+/* Inclusive prefix sums of x[0..n) in a fixed hierarchical order (a reading
+ * of Sec. II.B, which fixes only the normalisation S = sum w): runs of
+ * OR_FANOUT consecutive entries are summed sequentially (left to right, the
+ * first term taken as is); the run totals form a sequence that is summed the
+ * same way, recursively, until one run is left; entry j of run c is then
+ * Q_{c-1} + l_j, with l_j its sum inside the run and Q_{c-1} the inclusive
+ * prefix of the run totals before run c (entries of run 0 are l_j alone). */
+static void prefix_fixed_order(const double* x, int n, double* out)
+{
+    if (n <= OR_FANOUT) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) {
+            acc = (j == 0) ? x[j] : acc + x[j];
+            out[j] = acc;
+        }
+        return;
+    }
+    int m = (n + OR_FANOUT - 1) / OR_FANOUT;
+    double* tot = (double*)malloc(sizeof(double) * (size_t)m);
+    double* Q = (double*)malloc(sizeof(double) * (size_t)m);
+    for (int c = 0; c < m; ++c) {
+        int j0 = c * OR_FANOUT, j1 = j0 + OR_FANOUT < n ? j0 + OR_FANOUT : n;
+        double acc = 0.0;
+        for (int j = j0; j < j1; ++j) {
+            acc = (j == j0) ? x[j] : acc + x[j];
+            out[j] = acc;
+        }
+        tot[c] = acc;
+    }
+    prefix_fixed_order(tot, m, Q);
+    for (int j = OR_FANOUT; j < n; ++j) out[j] = Q[j / OR_FANOUT - 1] + out[j];
+    free(tot);
+    free(Q);
+}
+
+/* The cumulative weights the draws search: the fixed-order prefix sums made
+ * non-decreasing by a running maximum (exact in floating point; rounding in
+ * two different orders can leave the last sum of a run one unit above the
+ * first of the next), P_i = max_{j <= i} prefix_j.  S = P_{R-1}. */
+static void cumulative_weights(const double* w, int R, double* P)
+{
+    prefix_fixed_order(w, R, P);
+    for (int i = 1; i < R; ++i)
+        if (P[i] < P[i - 1]) P[i] = P[i - 1];
+}
+
+void or_weight_prefix(const double* w, int n, double* P_out, double* prefix_out)
+{
+    if (prefix_out) prefix_fixed_order(w, n, prefix_out);
+    cumulative_weights(w, n, P_out);
+}
 
 static double e_to_double(int kind, i128 v)
 {
@@ -409,18 +462,8 @@ static int resample_core2(int kind, int R, int Rn, const i128* E, double beta_pr
         if (E[r] < emin) emin = E[r];
     /* weights relative to the lowest energy: w_r = exp(-db (E_r - E_min)) */
     for (int r = 0; r < R; ++r) w[r] = or_spec_exp64(-(db * e_to_double(kind, E[r] - emin)));
-    /* prefix sums in a fixed order: sequential inside chunks of 1024, chunk
-     * offsets T accumulated sequentially, P_i = T_chunk(i) + L_i */
-    double T = 0.0;
-    for (int c0 = 0; c0 < R; c0 += OR_CHUNK) {
-        double Lsum = 0.0;
-        int c1 = c0 + OR_CHUNK < R ? c0 + OR_CHUNK : R;
-        for (int i = c0; i < c1; ++i) {
-            Lsum = (i == c0) ? w[i] : Lsum + w[i];
-            P[i] = T + Lsum;
-        }
-        T = T + Lsum;
-    }
+    /* cumulative weights in the fixed order, S their last entry */
+    cumulative_weights(w, R, P);
     double S = P[R - 1];
     *lnQ = (-(db * e_to_double(kind, emin)) + log(S)) - log((double)R);
     /* multinomial draws: parent of draw q = smallest i with u_q S < P_i */
@@ -471,16 +514,8 @@ static int resample_nearest(int kind, int R, double target, int cap, const i128*
     for (int r = 1; r < R; ++r)
         if (E[r] < emin) emin = E[r];
     for (int r = 0; r < R; ++r) w[r] = or_spec_exp64(-(db * e_to_double(kind, E[r] - emin)));
-    double T = 0.0;
-    for (int c0 = 0; c0 < R; c0 += OR_CHUNK) {
-        double Lsum = 0.0;
-        int c1 = c0 + OR_CHUNK < R ? c0 + OR_CHUNK : R;
-        for (int i = c0; i < c1; ++i) {
-            Lsum = (i == c0) ? w[i] : Lsum + w[i];
-            P[i] = T + Lsum;
-        }
-        T = T + Lsum;
-    }
+    /* cumulative weights in the fixed order, S their last entry */
+    cumulative_weights(w, R, P);
     double S = P[R - 1];
     *lnQ = (-(db * e_to_double(kind, emin)) + log(S)) - log((double)R);
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};

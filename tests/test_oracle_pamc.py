@@ -236,7 +236,7 @@ def test_zero_temperature_limit_is_greedy(oracle, kind):
 
 def test_resampling_components(oracle):
     rng = np.random.default_rng(41)
-    R = 2500  # three chunks of 1024, ragged last chunk
+    R = 2500  # three levels of runs of 32, ragged last runs
     E = rng.integers(-300, -100, R) * 4
     pairs = np.stack([E, np.where(E < 0, -1, 0)], 1).astype(np.int64).reshape(-1)
     b0, b1, k = 0.8, 0.85, 17
@@ -245,15 +245,26 @@ def test_resampling_components(oracle):
     ref_w = np.array([math.exp(-db * float(e - E.min())) for e in E])
     ulps = np.abs(res["w"].view(np.int64) - ref_w.view(np.int64))
     assert ulps.max() <= 2
-    # the stated summation order: sequential inside chunks of 1024, chunk offsets sequential
-    P = np.empty(R)
-    T = 0.0
-    for c0 in range(0, R, 1024):
-        acc = 0.0
-        for i in range(c0, min(c0 + 1024, R)):
-            acc = res["w"][i] if i == c0 else acc + res["w"][i]
-            P[i] = T + acc
-        T = T + acc
+    # the stated summation order: runs of 32 summed sequentially, recursively
+    # over the run totals, then a running maximum
+    def prefix(x):
+        out = []
+        if len(x) <= 32:
+            acc = 0.0
+            for j, v in enumerate(x):
+                acc = v if j == 0 else acc + v
+                out.append(acc)
+            return out
+        tot = []
+        for c0 in range(0, len(x), 32):
+            acc = 0.0
+            for j in range(c0, min(c0 + 32, len(x))):
+                acc = x[j] if j == c0 else acc + x[j]
+                out.append(acc)
+            tot.append(acc)
+        Q = prefix(tot)
+        return [v if j < 32 else Q[j // 32 - 1] + v for j, v in enumerate(out)]
+    P = np.maximum.accumulate(np.array(prefix([float(v) for v in res["w"]])))
     np.testing.assert_array_equal(res["P"], P)
     assert res["P"][-1] == pytest.approx(math.fsum(res["w"]), rel=1e-13)
     # brute force inverse CDF with a linear scan
