@@ -60,7 +60,7 @@ struct pa_ctx {
     int famcur;
     int32_t* counts;
     int32_t* blocksum;
-    double *w, *P, *tot, *T;
+    double *w, *P, *lev1, *bmax, *upper;
     StepAcc* acc;
     unsigned long long *cJ, *ch;
     int8_t* tmp8;
@@ -143,7 +143,7 @@ __global__ void acc0_kernel(StepAcc* acc, double betaF0, int R, int* Rdev)
 
 enum {
     W_J, W_H, W_JNEG, W_JFIX, W_HFIX, W_BETAS, W_S0, W_S1, W_E32, W_E128, W_PARENT, W_FAM0, W_FAM1,
-    W_COUNTS, W_BLOCKSUM, W_W, W_P, W_TOT, W_T, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
+    W_COUNTS, W_BLOCKSUM, W_W, W_P, W_LEV1, W_BMAX, W_UPPER, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
     W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_WTAB, W_SYNC, W_COUNT
 };
 
@@ -176,9 +176,9 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
     sz[W_BLOCKSUM] = sizeof(int32_t) * ((R + pa::kScanBlock - 1) / pa::kScanBlock + 1);
     sz[W_W] = sizeof(double) * (size_t)R;
     sz[W_P] = sizeof(double) * (size_t)R;
-    int nch = (R + pa::kChunk - 1) / pa::kChunk;
-    sz[W_TOT] = sizeof(double) * nch;
-    sz[W_T] = sizeof(double) * (nch + 1);
+    sz[W_LEV1] = sizeof(double) * (size_t)pa::rs_leaves(R);
+    sz[W_BMAX] = sizeof(double) * 2 * (size_t)pa::rs_wblocks(R);
+    sz[W_UPPER] = sizeof(double) * (size_t)pa::rs_upper_size(R);
     sz[W_ACC] = sizeof(StepAcc) * n_temps;
     sz[W_CJ] = acc_grad ? sizeof(unsigned long long) * (size_t)n_temps * D * N : 0;
     sz[W_CH] = acc_grad ? sizeof(unsigned long long) * (size_t)n_temps * N : 0;
@@ -411,7 +411,8 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->parent = (int32_t*)at(W_PARENT);
     c->fam[0] = (int32_t*)at(W_FAM0); c->fam[1] = (int32_t*)at(W_FAM1); c->famcur = 0;
     c->counts = (int32_t*)at(W_COUNTS); c->blocksum = (int32_t*)at(W_BLOCKSUM);
-    c->w = (double*)at(W_W); c->P = (double*)at(W_P); c->tot = (double*)at(W_TOT); c->T = (double*)at(W_T);
+    c->w = (double*)at(W_W); c->P = (double*)at(W_P);
+    c->lev1 = (double*)at(W_LEV1); c->bmax = (double*)at(W_BMAX); c->upper = (double*)at(W_UPPER);
     c->acc = (StepAcc*)at(W_ACC);
     c->cJ = c->acc_grad ? (unsigned long long*)at(W_CJ) : nullptr;
     c->ch = c->acc_grad ? (unsigned long long*)at(W_CH) : nullptr;
@@ -600,7 +601,7 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         }
         ra.E32 = c->E32; ra.E128 = c->E128;
         ra.prev = c->acc + (k - 1); ra.cur = c->acc + k;
-        ra.w = c->w; ra.P = c->P; ra.tot = c->tot; ra.T = c->T;
+        ra.w = c->w; ra.P = c->P; ra.lev1 = c->lev1; ra.bmax = c->bmax; ra.upper = c->upper;
         ra.counts = c->counts; ra.blocksum = c->blocksum; ra.parent = c->parent;
         ra.fam_in = c->fam[c->famcur]; ra.fam_out = c->fam[c->famcur ^ 1];
         ra.dbeta = c->betas[k] - c->betas[k - 1];
@@ -1498,7 +1499,7 @@ static int batch_enqueue(pa_batch* b, bool allow_tune)
         }
     } else {
         PB_CK(b, pa::launch_resample_batched(b->d_rs + (size_t)k * b->n_inst, b->n_inst, b->maxR, b->st));
-        b->launches += 7;
+        b->launches += 8;
     }
     if (!b->tuned && allow_tune && k >= 1) {
         int rc = batch_tune(b, k);
@@ -1510,7 +1511,7 @@ static int batch_enqueue(pa_batch* b, bool allow_tune)
     PB_CK(b, pa::launch_sweep_batched(ps, rs, b->d_sw + (size_t)k * b->n_inst, b->d_items[b->mult - 1],
                                       b->n_items[b->mult - 1], b->mult, b->d_counters + k, b->blocks,
                                       b->smem[b->mult - 1], b->st));
-    PB_CK(b, pa::launch_observe_batched(b->d_ob + (size_t)k * b->n_inst, b->n_inst, b->st));
+    PB_CK(b, pa::launch_observe_batched(b->d_ob + (size_t)k * b->n_inst, b->n_inst, b->maxR, b->st));
     b->launches += 3;
     for (int i = 0; i < b->n_inst; ++i) {
         pa_ctx* c = b->ctx[i];

@@ -150,12 +150,17 @@ struct ResampleArgs {
     const double* wtab;          // +-J: weight per level (E - E_min) / 4, or null
     int wtab_n;                  // levels in wtab
     // two zeroed block counters: with them the last block of the weights
-    // launch sums the chunk offsets and the last block of the block-sum launch
-    // scans the block sums (no separate launches); null: separate launches
+    // launch completes the prefix (upper levels, run offsets, running maximum,
+    // S, ln Q) and the last block of the block-sum launch scans the block sums
+    // (no separate launches); null: separate launches
     int* sync;
-    double* P;                   // [R] local prefix, then P
-    double* tot;                 // [nchunks] chunk sums
-    double* T;                   // [nchunks + 1] chunk offsets
+    double* P;                   // [R] sums inside runs of 32, then the cumulative weights
+                                 // up to the running maximum over earlier weights blocks
+    double* lev1;                // [rs_leaves(R)] level-1 sums inside runs of 32 runs, then
+                                 // the inclusive prefix of the run totals
+    double* bmax;                // [2 rs_wblocks(R)] largest prefix sum of each weights block,
+                                 // then the largest before each block (running maximum)
+    double* upper;               // [rs_upper_size(R)] levels 2, 3, ... of the prefix
     int32_t* counts;             // [R] copy numbers (zero on entry, zeroed again on exit)
     int32_t* blocksum;           // [nblocks] scratch for the count scan
     int32_t* parent;             // [R] out
@@ -165,7 +170,23 @@ struct ResampleArgs {
     int k;
     uint32_t key0, key1, c3;
 };
-constexpr int kChunk = 1024;     // fixed summation chunk of the weight prefix
+// Weight prefix in a fixed order of fan-out kFan: runs of kFan weights summed
+// left to right, the run totals likewise, recursively; each weights block
+// covers kFan runs (kFan^2 weights, levels 0 and 1).
+constexpr int kFan = 32;
+constexpr int kWBlock = kFan * kFan;
+__host__ __device__ constexpr inline int rs_leaves(int R) { return (R + kFan - 1) / kFan; }
+__host__ __device__ constexpr inline int rs_wblocks(int R) { return (R + kWBlock - 1) / kWBlock; }
+// doubles of the levels >= 2 (block totals, then their run totals, ...)
+__host__ __device__ constexpr inline int rs_upper_size(int R)
+{
+    int n = rs_wblocks(R), t = 0;
+    for (;;) {
+        t += n;
+        if (n <= kFan) return t;
+        n = (n + kFan - 1) / kFan;
+    }
+}
 constexpr int kScanBlock = 4096; // elements per block of the copy-number scan
 cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st);
 // all instances of a batch at once: tab[i] describes instance i (device memory)
@@ -175,7 +196,13 @@ struct ObsPartial {
     long long sumE, sumE2, min_lo, min_hi;
     double sumEd, sumE2d, clnc, pad;
 };
-constexpr int kObsBlocks = 64;   // fixed partition of the observables reduction
+constexpr int kObsBlocks = 608;  // most blocks of the observables reduction (4 per SM of GB300)
+// blocks of the observables reduction for a population of R: about 4096
+// replicas each, at most kObsBlocks (a function of R only)
+__host__ __device__ constexpr inline int obs_blocks(int R)
+{
+    return R <= 4096 ? 1 : ((R + 4095) / 4096 > kObsBlocks ? kObsBlocks : (R + 4095) / 4096);
+}
 struct ObsArgs {
     int R, kind;
     const int* Rdev;             // population in device memory (or null: R)
@@ -187,7 +214,7 @@ struct ObsArgs {
     int* sync;                   // zeroed block counter: the last block combines (or null)
 };
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st);
-cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, cudaStream_t st);
+cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, int maxR, cudaStream_t st);
 cudaError_t launch_grad_backward(const unsigned long long* cJ, const unsigned long long* ch,
                                  const double* gbar, const double* betas, const double* Rk,
                                  int n_temps, int nJ, int N, double* dJ, double* dh, cudaStream_t st);

@@ -24,7 +24,8 @@
 namespace {
 
 constexpr int kMaxR = PA_STATIC_MAX_R;
-constexpr int kMaxChunks = (kMaxR + pa::kChunk - 1) / pa::kChunk;
+constexpr int kMaxLeaves = (kMaxR + pa::kFan - 1) / pa::kFan;
+constexpr int kMaxUpper = 2 * ((kMaxR + pa::kWBlock - 1) / pa::kWBlock) + 64;  // levels >= 2
 constexpr int kMaxScanBlocks = (kMaxR + pa::kScanBlock - 1) / pa::kScanBlock;
 
 // carve-up of the scratch array (byte offsets, each 256-byte aligned)
@@ -34,12 +35,14 @@ constexpr size_t kOffP = kOffW + al(sizeof(double) * kMaxR);
 constexpr size_t kOffCounts = kOffP + al(sizeof(double) * kMaxR);
 constexpr size_t kOffFamIn = kOffCounts + al(sizeof(int32_t) * kMaxR);
 constexpr size_t kOffFamOut = kOffFamIn + al(sizeof(int32_t) * kMaxR);
-constexpr size_t kOffTot = kOffFamOut + al(sizeof(int32_t) * kMaxR);
-constexpr size_t kOffT = kOffTot + al(sizeof(double) * kMaxChunks);
-constexpr size_t kOffBlock = kOffT + al(sizeof(double) * (kMaxChunks + 1));
+constexpr size_t kOffLev1 = kOffFamOut + al(sizeof(int32_t) * kMaxR);
+constexpr size_t kOffBmax = kOffLev1 + al(sizeof(double) * kMaxLeaves);
+constexpr size_t kOffUpper = kOffBmax + al(sizeof(double) * 2 * ((kMaxR + pa::kWBlock - 1) / pa::kWBlock));
+constexpr size_t kOffBlock = kOffUpper + al(sizeof(double) * kMaxUpper);
 constexpr size_t kOffAcc = kOffBlock + al(sizeof(int32_t) * (kMaxScanBlocks + 1));
 constexpr size_t kBytes = kOffAcc + al(2 * sizeof(pa::StepAcc));
 static_assert(kBytes <= PA_STATIC_SCRATCH_BYTES, "scratch layout exceeds the stated size");
+static_assert(pa::rs_upper_size(kMaxR) <= kMaxUpper, "upper prefix levels fit");
 
 }  // namespace
 
@@ -140,8 +143,9 @@ extern "C" int pa_resample_static(const int32_t* d_E, int R, double beta_prev, d
     ra.cur = reinterpret_cast<pa::StepAcc*>(base + kOffAcc) + 1;
     ra.w = reinterpret_cast<double*>(base + kOffW);
     ra.P = reinterpret_cast<double*>(base + kOffP);
-    ra.tot = reinterpret_cast<double*>(base + kOffTot);
-    ra.T = reinterpret_cast<double*>(base + kOffT);
+    ra.lev1 = reinterpret_cast<double*>(base + kOffLev1);
+    ra.bmax = reinterpret_cast<double*>(base + kOffBmax);
+    ra.upper = reinterpret_cast<double*>(base + kOffUpper);
     ra.counts = reinterpret_cast<int32_t*>(base + kOffCounts);
     ra.blocksum = reinterpret_cast<int32_t*>(base + kOffBlock);
     ra.parent = d_parent;

@@ -6,12 +6,16 @@
 // -(beta'-beta) E_min + ln S - ln R and beta F_k = -N ln 2 - sum_{l<=k} ln Q_l.
 //
 // Fixed order, so that the draws do not depend on the launch geometry:
-//   P_i = T_c + L_i, L_i the sequential inclusive sum of w inside chunk
-//   c = i / 1024, T_0 = 0, T_{c+1} = T_c + L_last(c); S = P_{R-1}.
-// Draw q (RES stream) picks the smallest i with u_q S < P_i (if u_q S == S
-// after rounding: the smallest i with P_i >= u_q S).  Copy numbers are exact
-// integer counts; their exclusive scan places the copies of replica i in
-// slots [C_i, C_i + n_i), so families stay contiguous (Sec. V.A).
+// runs of 32 weights are summed left to right; the run totals are summed the
+// same way, recursively, until one run is left; entry j of run c is
+// Q_{c-1} + l_j (l_j its sum inside the run, Q the inclusive prefix of the
+// run totals; run 0: l_j alone).  P_i is the running maximum of those sums
+// (exact; it only repairs the one-unit steps that two summation orders can
+// leave at a run boundary) and S = P_{R-1}.  Draw q (RES stream) picks the
+// smallest i with u_q S < P_i (if u_q S == S after rounding: the smallest i
+// with P_i >= u_q S).  Copy numbers are exact integer counts; their exclusive
+// scan places the copies of replica i in slots [C_i, C_i + n_i), so families
+// stay contiguous (Sec. V.A).
 #include "pa_device.cuh"
 #include "pa_internal.h"
 
@@ -50,44 +54,64 @@ __device__ __forceinline__ bool last_block(int* counter)
 // source population: in device memory for the nearest-integer scheme
 __device__ __forceinline__ int rs_src(const ResampleArgs& a) { return a.Rsrc ? *a.Rsrc : a.R; }
 
-// weights and chunk-local sequential prefix sums (one block per chunk)
-__device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int c)
+// Weights and the two lowest levels of the prefix, one block of kWBlock
+// threads per kWBlock weights.  GB300 has little FP64 throughput, so every
+// addition of the specified order is executed once: lane c of warp 0 sums
+// run c (32 weights, staged in shared memory) left to right, then lane 0
+// sums the block's run totals left to right.
+__device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int b)
 {
-    __shared__ double wsh[kChunk];
-    const int i0 = c * kChunk;
-    const int n = min(kChunk, rs_src(a) - i0);
-    if (n <= 0) return;  // block-uniform: past the source population
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    __shared__ double s_w[kFan * (kFan + 1)];  // run c at [c (kFan + 1)], padded against bank conflicts
+    __shared__ double s_t[kFan];
+    const int R = rs_src(a);
+    const int i0 = b * kWBlock;
+    if (i0 >= R) return;  // block-uniform: past the source population
+    const int tid = threadIdx.x;
+    const int n = min(kWBlock, R - i0);
+    const int i = i0 + tid;
+    if (tid < n) {
         double w;
-        const int lv = a.kind == 0 ? a.E32[i0 + t] - (int)a.prev->emin_lo : 0;
+        const int lv = a.kind == 0 ? a.E32[i] - (int)a.prev->emin_lo : 0;
         if (a.wtab && (lv & 3) == 0 && (lv >> 2) < a.wtab_n) {
             w = a.wtab[lv >> 2];  // +-J: E - E_min is a multiple of 4, the weight a table entry
         } else {
-            const double d = e_minus_min_to_double(a, i0 + t);
+            const double d = e_minus_min_to_double(a, i);
             w = spec_exp64(-__dmul_rn(a.dbeta, d));
         }
-        wsh[t] = w;
-        a.w[i0 + t] = w;
+        a.w[i] = w;
+        s_w[(tid / kFan) * (kFan + 1) + tid % kFan] = w;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double acc = wsh[0];
-        for (int t = 1; t < n; ++t) {
-            acc = __dadd_rn(acc, wsh[t]);
-            wsh[t] = acc;
+    const int nruns = (n + kFan - 1) / kFan;
+    if (tid < nruns) {  // run tid, left to right
+        double* x = s_w + tid * (kFan + 1);
+        const int cnt = min(kFan, n - tid * kFan);
+        double acc = x[0];
+        for (int j = 1; j < cnt; ++j) {
+            acc = __dadd_rn(acc, x[j]);
+            x[j] = acc;
         }
-        a.tot[c] = acc;
+        s_t[tid] = acc;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < n; t += blockDim.x) a.P[i0 + t] = wsh[t];
+    if (tid < n) a.P[i] = s_w[(tid / kFan) * (kFan + 1) + tid % kFan];
+    if (tid == 0) {  // the block's run totals, left to right
+        double acc = s_t[0];
+        a.lev1[b * kFan] = acc;
+        for (int c = 1; c < nruns; ++c) {
+            acc = __dadd_rn(acc, s_t[c]);
+            a.lev1[b * kFan + c] = acc;
+        }
+        a.upper[b] = acc;
+    }
 }
-__device__ __forceinline__ void rs_offsets_body(const ResampleArgs& a);
-__global__ void __launch_bounds__(256) rs_weights_kernel(ResampleArgs a)
+__device__ __forceinline__ void rs_top_body(const ResampleArgs& a);
+__global__ void __launch_bounds__(kWBlock) rs_weights_kernel(ResampleArgs a)
 {
     rs_weights_body(a, blockIdx.x);
-    if (a.sync && last_block(a.sync) && threadIdx.x < 32) rs_offsets_body(a);  // chunk offsets
+    if (a.sync && last_block(a.sync)) rs_top_body(a);  // levels >= 2 of the prefix
 }
-__global__ void __launch_bounds__(256) rs_weights_batched(const ResampleArgs* tab)
+__global__ void __launch_bounds__(kWBlock) rs_weights_batched(const ResampleArgs* tab)
 {
     const ResampleArgs& a = tab[blockIdx.y];
     rs_weights_body(a, blockIdx.x);
@@ -102,30 +126,141 @@ __global__ void rs_table_kernel(ResampleArgs a)
     if (l < a.wtab_n) const_cast<double*>(a.wtab)[l] = spec_exp64(-__dmul_rn(a.dbeta, (double)(4 * l)));
 }
 
-// chunk offsets (sequential), S, ln Q, running free energy.  One warp: the
-// chunk sums are staged in shared memory 1024 at a time (coalesced loads),
-// lane 0 adds them in chunk order.
-__device__ __forceinline__ void rs_offsets_body(const ResampleArgs& a)
+// Levels >= 2 of the prefix, by one block of kWBlock threads after every
+// weights block is done: bottom-up sums inside runs of the block totals (each
+// thread loads its run, then adds in order), then top-down Q_{c-1} + l_j.
+__device__ __forceinline__ void rs_top_body(const ResampleArgs& a)
 {
-    __shared__ double tsh[1024];
-    const int lane = threadIdx.x & 31;
+    constexpr int kMaxLev = 8;  // kFan^(kMaxLev+1) > 2^31 weights
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int R = rs_src(a);
-    const int nchunks = (R + kChunk - 1) / kChunk;
-    double T = 0.0;
-    for (int c0 = 0; c0 < nchunks; c0 += 1024) {
-        const int n = min(1024, nchunks - c0);
-        for (int c = lane; c < n; c += 32) tsh[c] = a.tot[c0 + c];
-        __syncwarp();
-        if (lane == 0)
-            for (int c = 0; c < n; ++c) {
-                a.T[c0 + c] = T;
-                T = __dadd_rn(T, tsh[c]);
+    int base[kMaxLev], len[kMaxLev], nl = 0;
+    int n = rs_wblocks(R), off = 0;
+    for (;;) {
+        base[nl] = off; len[nl] = n; ++nl;
+        const int nc = n <= kFan ? 1 : (n + kFan - 1) / kFan;
+        for (int c = tid; c < nc; c += nt) {
+            double* x = a.upper + off + c * kFan;
+            const int cnt = min(kFan, n - c * kFan);
+            double acc = 0.0;
+            for (int j0 = 0; j0 < cnt; j0 += 8) {  // eight independent loads, then the additions
+                double v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = j0 + j < cnt ? x[j0 + j] : 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    acc = (j0 + j == 0) ? v[0] : __dadd_rn(acc, v[j]);  // +0 past the run: no change
+                    v[j] = acc;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j0 + j < cnt) x[j0 + j] = v[j];
             }
-        __syncwarp();
+            if (n > kFan) a.upper[off + n + c] = acc;
+        }
+        __syncthreads();
+        if (n <= kFan) break;  // one run left: its sums are the prefix of this level
+        off += n;
+        n = nc;
     }
-    if (lane != 0) return;
-    a.T[nchunks] = T;
-    const double S = T;
+    for (int v = nl - 2; v >= 0; --v) {
+        double* x = a.upper + base[v];
+        const double* q = a.upper + base[v + 1];
+        for (int j = kFan + tid; j < len[v]; j += nt) x[j] = __dadd_rn(q[j / kFan - 1], x[j]);
+        __syncthreads();
+    }
+}
+__global__ void __launch_bounds__(kWBlock) rs_top_kernel(ResampleArgs a) { rs_top_body(a); }
+// one block per instance
+__global__ void __launch_bounds__(kWBlock) rs_top_batched(const ResampleArgs* tab, int n_inst)
+{
+    if ((int)blockIdx.x < n_inst) rs_top_body(tab[blockIdx.x]);
+}
+
+// Non-negative doubles compare as their bit patterns do (as signed 64-bit
+// integers): maxima and the draw search use the integer compare, which is
+// exact and leaves GB300's scarce FP64 units to the specified additions.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// Level 0 and the running maximum inside one weights block: weight i of run
+// c gets Q1_{c-1} + l_i (Q1_{c-1} = Q2_{b'-1} + l1_{c-1} with b' the block of
+// run c - 1, the level-1 sums alone in block 0), then P_i = the largest of
+// these up to i within the block; bmax[b] = the block's largest.
+__device__ __forceinline__ void rs_finalize_body(const ResampleArgs& a, int b)
+{
+    __shared__ double s_q[kFan];
+    __shared__ long long s_m[32];
+    const int R = rs_src(a);
+    const int i0 = b * kWBlock;
+    if (i0 >= R) return;  // block-uniform
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < kFan) {  // Q1 of the run before run c = b kFan + tid (one addition per run)
+        const int c = b * kFan + tid;
+        double q = 0.0;
+        if (c > 0 && c * kFan < R) {
+            const int cb = (c - 1) / kFan;
+            const double l1 = a.lev1[c - 1];
+            q = cb == 0 ? l1 : __dadd_rn(a.upper[cb - 1], l1);
+        }
+        s_q[tid] = q;
+    }
+    __syncthreads();
+    const int i = i0 + tid;
+    long long m = 0;  // bits of +0.0: weights are >= 0
+    if (i < R) {
+        const double l = a.P[i];
+        m = dbits(i < kFan ? l : __dadd_rn(s_q[tid / kFan], l));
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, m, o);
+        if (lane >= o) m = max(m, v);
+    }
+    if (lane == 31) s_m[warp] = m;
+    __syncthreads();
+    long long before = 0;
+    for (int v = 0; v < warp; ++v) before = max(before, s_m[v]);
+    if (i < R) a.P[i] = __longlong_as_double(max(before, m));
+    if (tid == 0) {
+        long long bm = 0;
+        for (int v = 0; v < 32; ++v) bm = max(bm, s_m[v]);
+        a.bmax[b] = __longlong_as_double(bm);
+    }
+}
+// running maximum over the weights blocks (bmax[nb + b] = the largest
+// cumulative weight before block b), S = the largest cumulative weight, ln Q
+// and the running free energy; one block of kWBlock threads, kWBlock block
+// maxima per pass (integer maxima of the bit patterns)
+__device__ __forceinline__ void rs_blockmax_body(const ResampleArgs& a)
+{
+    __shared__ long long s_w[32];
+    __shared__ long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int R = rs_src(a);
+    const int nb = rs_wblocks(R);
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += kWBlock) {
+        const int b = b0 + tid;
+        long long m = b < nb ? dbits(a.bmax[b]) : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, m, o);
+            if (lane >= o) m = max(m, u);
+        }
+        if (lane == 31) s_w[warp] = m;
+        const long long carry = s_carry;
+        __syncthreads();
+        long long before = carry;
+        for (int w = 0; w < warp; ++w) before = max(before, s_w[w]);
+        const long long up = __shfl_up_sync(0xffffffffu, m, 1);
+        const long long excl = lane > 0 ? max(before, up) : before;
+        if (b < nb) a.bmax[nb + b] = __longlong_as_double(excl);
+        if (tid == kWBlock - 1) s_carry = max(before, m);
+        __syncthreads();
+    }
+    if (tid != 0) return;
+    const double S = __longlong_as_double(s_carry);
     double emin_d;
     if (a.kind == 0) {
         emin_d = (double)(int)a.prev->emin_lo;
@@ -141,54 +276,89 @@ __device__ __forceinline__ void rs_offsets_body(const ResampleArgs& a)
     a.cur->betaF = __dsub_rn(a.betaF0, sum);
     a.cur->S = S;
 }
-__global__ void rs_offsets_kernel(ResampleArgs a)
+__global__ void __launch_bounds__(kWBlock) rs_finalize_kernel(ResampleArgs a)
 {
-    if (threadIdx.x < 32 && blockIdx.x == 0) rs_offsets_body(a);
+    rs_finalize_body(a, blockIdx.x);
+    if (a.sync && last_block(a.sync + 3)) rs_blockmax_body(a);
 }
-// one warp per instance
-__global__ void rs_offsets_batched(const ResampleArgs* tab, int n_inst)
+__global__ void __launch_bounds__(kWBlock) rs_finalize_batched(const ResampleArgs* tab)
 {
-    const int i = blockIdx.x;
-    if (i < n_inst && threadIdx.x < 32) rs_offsets_body(tab[i]);
+    rs_finalize_body(tab[blockIdx.y], blockIdx.x);
 }
-
-__device__ __forceinline__ void rs_finalize_body(const ResampleArgs& a, int i)
+__global__ void __launch_bounds__(kWBlock) rs_blockmax_kernel(ResampleArgs a) { rs_blockmax_body(a); }
+// one block per instance
+__global__ void __launch_bounds__(kWBlock) rs_blockmax_batched(const ResampleArgs* tab, int n_inst)
 {
-    if (i < rs_src(a)) a.P[i] = __dadd_rn(a.T[i / kChunk], a.P[i]);
-}
-__global__ void rs_finalize_kernel(ResampleArgs a) { rs_finalize_body(a, blockIdx.x * blockDim.x + threadIdx.x); }
-__global__ void rs_finalize_batched(const ResampleArgs* tab)
-{
-    rs_finalize_body(tab[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+    if ((int)blockIdx.x < n_inst) rs_blockmax_body(tab[blockIdx.x]);
 }
 
+// Multinomial draws.  P is non-decreasing, so the smallest i with x < P_i
+// lies in the first segment (of s consecutive weights, whole weights blocks)
+// whose last P exceeds x: each block stages the segment ends in shared memory,
+// finds the segment there and bisects only inside it in global memory.  P_i
+// is the stored block-local value raised to the largest value before its
+// weights block.
+constexpr int kDrawThreads = 512;
+constexpr int kMaxSeg = 2048;
+__device__ __forceinline__ int rs_seg_blocks(int nb)
+{
+    int s = 1;
+    while ((nb + s - 1) / s > kMaxSeg) s *= 2;
+    return s;
+}
+__device__ __forceinline__ long long rs_P(const ResampleArgs& a, int nb, int i)
+{
+    return max(dbits(a.bmax[nb + i / kWBlock]), dbits(a.P[i]));
+}
 __device__ __forceinline__ void rs_draws_body(const ResampleArgs& a, int q)
 {
+    __shared__ long long s_end[kMaxSeg];
+    const int R = a.R;
+    const int nb = rs_wblocks(R);
+    const int sb = rs_seg_blocks(nb), seg = sb * kWBlock, nseg = (nb + sb - 1) / sb;
+    const double S = a.cur->S;
+    for (int k = threadIdx.x; k < nseg; k += blockDim.x) {
+        const int lb = min(nb - 1, k * sb + sb - 1);  // last weights block of segment k
+        // its largest P: the largest before the next block, or S for the last block
+        s_end[k] = lb + 1 < nb ? dbits(a.bmax[nb + lb + 1]) : dbits(S);
+    }
+    __syncthreads();
     if (q >= a.Rn) return;
-    const int nchunks = (a.R + kChunk - 1) / kChunk;
     const u32x4 o = philox((uint32_t)q, (uint32_t)a.k, 0u, a.c3, a.key0, a.key1);
-    const double S = a.T[nchunks];
-    const double x = __dmul_rn(uniform53(o.x, o.y), S);
-    const double* __restrict__ P = a.P;
-    int lo = 0, hi = a.R;
+    const long long x = dbits(__dmul_rn(uniform53(o.x, o.y), S));  // x >= 0
+    int lo = 0, hi = nseg;  // first segment whose end exceeds x
     while (lo < hi) {
         const int mid = lo + ((hi - lo) >> 1);
-        if (x < P[mid]) hi = mid; else lo = mid + 1;
+        if (x < s_end[mid]) hi = mid; else lo = mid + 1;
     }
-    if (lo == a.R) {
-        lo = 0; hi = a.R;
+    if (lo < nseg) {
+        const int k = lo;
+        lo = k * seg;
+        hi = min(R - 1, k * seg + seg - 1);  // x < P[hi]
         while (lo < hi) {
             const int mid = lo + ((hi - lo) >> 1);
-            if (P[mid] >= x) hi = mid; else lo = mid + 1;
+            if (x < rs_P(a, nb, mid)) hi = mid; else lo = mid + 1;
         }
-        if (lo >= a.R) lo = a.R - 1;  // unreachable: x = u S <= S = P[R-1]
+    } else {
+        // x == S after rounding: the smallest i with P_i >= x
+        lo = 0; hi = R;
+        while (lo < hi) {
+            const int mid = lo + ((hi - lo) >> 1);
+            if (rs_P(a, nb, mid) >= x) hi = mid; else lo = mid + 1;
+        }
+        if (lo >= R) lo = R - 1;  // unreachable: x = u S <= S = P[R-1]
     }
     atomicAdd(&a.counts[lo], 1);
 }
-__global__ void rs_draws_kernel(ResampleArgs a) { rs_draws_body(a, blockIdx.x * blockDim.x + threadIdx.x); }
-__global__ void rs_draws_batched(const ResampleArgs* tab)
+__global__ void __launch_bounds__(kDrawThreads) rs_draws_kernel(ResampleArgs a)
 {
-    rs_draws_body(tab[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+    rs_draws_body(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+__global__ void __launch_bounds__(kDrawThreads) rs_draws_batched(const ResampleArgs* tab)
+{
+    const ResampleArgs& a = tab[blockIdx.y];
+    if ((int)(blockIdx.x * blockDim.x) >= a.Rn) return;  // block-uniform: no draw of this instance
+    rs_draws_body(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // nearest-integer copy numbers (Sec. II.B, population in expectation):
@@ -198,8 +368,7 @@ __device__ __forceinline__ void rs_nearest_body(const ResampleArgs& a, int i)
 {
     const int R = rs_src(a);
     if (i >= R) return;
-    const int nchunks = (R + kChunk - 1) / kChunk;
-    const double S = a.T[nchunks];
+    const double S = a.cur->S;
     const u32x4 o = philox((uint32_t)i, (uint32_t)a.k, 1u, a.c3, a.key0, a.key1);
     const double u = uniform53(o.x, o.y);
     const double tau = __ddiv_rn(__dmul_rn(a.target, a.w[i]), S);
@@ -331,16 +500,16 @@ __global__ void __launch_bounds__(1024) rs_fill_batched(const ResampleArgs* tab)
 
 cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
 {
-    const int nchunks = (a.R + kChunk - 1) / kChunk;
     const int nb = (a.R + kScanBlock - 1) / kScanBlock;
     if (a.wtab) rs_table_kernel<<<(a.wtab_n + 255) / 256, 256, 0, st>>>(a);
-    rs_weights_kernel<<<nchunks, 256, 0, st>>>(a);
-    if (!a.sync) rs_offsets_kernel<<<1, 32, 0, st>>>(a);
-    rs_finalize_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
+    rs_weights_kernel<<<rs_wblocks(a.R), kWBlock, 0, st>>>(a);
+    if (!a.sync) rs_top_kernel<<<1, kWBlock, 0, st>>>(a);
+    rs_finalize_kernel<<<rs_wblocks(a.R), kWBlock, 0, st>>>(a);
+    if (!a.sync) rs_blockmax_kernel<<<1, kWBlock, 0, st>>>(a);
     if (a.scheme == 1)
         rs_nearest_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
     else
-        rs_draws_kernel<<<(a.Rn + 255) / 256, 256, 0, st>>>(a);
+        rs_draws_kernel<<<(a.Rn + kDrawThreads - 1) / kDrawThreads, kDrawThreads, 0, st>>>(a);
     rs_blocksum_kernel<<<nb, 1024, 0, st>>>(a);
     if (!a.sync) rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a);
     rs_fill_kernel<<<nb, 1024, 0, st>>>(a);
@@ -349,13 +518,13 @@ cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
 
 cudaError_t launch_resample_batched(const ResampleArgs* tab, int n_inst, int maxR, cudaStream_t st)
 {
-    const unsigned nchunks = (maxR + kChunk - 1) / kChunk;
     const unsigned nb = (maxR + kScanBlock - 1) / kScanBlock;
     const unsigned ni = (unsigned)n_inst;
-    rs_weights_batched<<<dim3(nchunks, ni), 256, 0, st>>>(tab);
-    rs_offsets_batched<<<ni, 32, 0, st>>>(tab, n_inst);
-    rs_finalize_batched<<<dim3((maxR + 255) / 256, ni), 256, 0, st>>>(tab);
-    rs_draws_batched<<<dim3((maxR + 255) / 256, ni), 256, 0, st>>>(tab);
+    rs_weights_batched<<<dim3(rs_wblocks(maxR), ni), kWBlock, 0, st>>>(tab);
+    rs_top_batched<<<ni, kWBlock, 0, st>>>(tab, n_inst);
+    rs_finalize_batched<<<dim3(rs_wblocks(maxR), ni), kWBlock, 0, st>>>(tab);
+    rs_blockmax_batched<<<ni, kWBlock, 0, st>>>(tab, n_inst);
+    rs_draws_batched<<<dim3((maxR + kDrawThreads - 1) / kDrawThreads, ni), kDrawThreads, 0, st>>>(tab);
     rs_blocksum_batched<<<dim3(nb, ni), 1024, 0, st>>>(tab);
     rs_scan_blocks_batched<<<(ni + 63) / 64, 64, 0, st>>>(tab, n_inst);
     rs_fill_batched<<<dim3(nb, ni), 1024, 0, st>>>(tab);
@@ -373,7 +542,9 @@ __device__ __forceinline__ void observe_partial_body(const ObsArgs& a)
     __shared__ __int128 s_min[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = a.Rdev ? *a.Rdev : a.R;
-    const int per = (R + kObsBlocks - 1) / kObsBlocks;
+    const int nb = obs_blocks(R);
+    if ((int)blockIdx.x >= nb) return;  // block-uniform
+    const int per = (R + nb - 1) / nb;
     const int j0 = blockIdx.x * per, j1 = min(R, j0 + per);
     long long se = 0, se2 = 0;
     double sed = 0.0, se2d = 0.0, clnc = 0.0;
@@ -394,26 +565,44 @@ __device__ __forceinline__ void observe_partial_body(const ObsArgs& a)
         }
         const int f = a.family[j];
         if (j == 0 || a.family[j - 1] != f) {
-            int lo = j + 1, hi = R;  // first index with family > f (families are sorted)
-            while (lo < hi) {
-                const int mid = lo + ((hi - lo) >> 1);
-                if (a.family[mid] > f) hi = mid; else lo = mid + 1;
+            // end of the run of family f (families are sorted): a short
+            // forward look first, bisection for long runs
+            int e = j + 1;
+            while (e < R && e < j + 8 && a.family[e] == f) ++e;
+            if (e < R && a.family[e] == f) {
+                int lo = e + 1, hi = R;  // first index with family > f
+                while (lo < hi) {
+                    const int mid = lo + ((hi - lo) >> 1);
+                    if (a.family[mid] > f) hi = mid; else lo = mid + 1;
+                }
+                e = lo;
             }
-            const double c = (double)(lo - j);
+            const double c = (double)(e - j);
             clnc = __fma_rn(c, log(c), clnc);
         }
     }
+    // fixed shuffle trees; the FP64 ones only where they can add something
+    // (GB300 has little FP64 throughput): +-J energies are integer sums, and a
+    // warp without a family start has clnc = 0 in every lane
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         se += __shfl_down_sync(0xffffffffu, se, off);
         se2 += __shfl_down_sync(0xffffffffu, se2, off);
-        sed = __dadd_rn(sed, __shfl_down_sync(0xffffffffu, sed, off));
-        se2d = __dadd_rn(se2d, __shfl_down_sync(0xffffffffu, se2d, off));
-        clnc = __dadd_rn(clnc, __shfl_down_sync(0xffffffffu, clnc, off));
         const long long lo = __shfl_down_sync(0xffffffffu, (long long)(unsigned long long)mn, off);
         const long long hi = __shfl_down_sync(0xffffffffu, (long long)(mn >> 64), off);
         const __int128 o = ((__int128)hi << 64) | (unsigned long long)lo;
         if (o < mn) mn = o;
+    }
+    if (a.kind != 0) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sed = __dadd_rn(sed, __shfl_down_sync(0xffffffffu, sed, off));
+            se2d = __dadd_rn(se2d, __shfl_down_sync(0xffffffffu, se2d, off));
+        }
+    }
+    if (__any_sync(0xffffffffu, clnc != 0.0)) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) clnc = __dadd_rn(clnc, __shfl_down_sync(0xffffffffu, clnc, off));
     }
     if (lane == 0) {
         s_ll[0][warp] = se; s_ll[1][warp] = se2;
@@ -440,25 +629,43 @@ __device__ __forceinline__ void observe_final_body(const ObsArgs& a);
 __global__ void __launch_bounds__(1024) observe_partial_kernel(ObsArgs a)
 {
     observe_partial_body(a);
-    if (a.sync && last_block(a.sync) && threadIdx.x == 0) observe_final_body(a);  // combine in block order
+    if (a.sync && last_block(a.sync) && threadIdx.x < 32) observe_final_body(a);  // combine in a fixed order
 }
 __global__ void __launch_bounds__(1024) observe_partial_batched(const ObsArgs* tab)
 {
     observe_partial_body(tab[blockIdx.y]);
 }
 
+// partials combined by one warp: lane l adds blocks l, l + 32, ... in order,
+// then the 32 lane sums are added by a fixed shuffle tree (the same order on
+// every GPU)
 __device__ __forceinline__ void observe_final_body(const ObsArgs& a)
 {
+    const int lane = threadIdx.x & 31;
     long long A = 0, B = 0;
     double C = 0.0, Dd = 0.0, F = 0.0;
     __int128 M = (__int128)(((unsigned __int128)1 << 127) - 1);
-    for (int b = 0; b < kObsBlocks; ++b) {
+    const int nb = obs_blocks(a.Rdev ? *a.Rdev : a.R);
+    for (int b = lane; b < nb; b += 32) {
         const ObsPartial p = a.part[b];
         A += p.sumE; B += p.sumE2;
         C = __dadd_rn(C, p.sumEd); Dd = __dadd_rn(Dd, p.sumE2d); F = __dadd_rn(F, p.clnc);
         const __int128 m = ((__int128)p.min_hi << 64) | (unsigned long long)p.min_lo;
         if (m < M) M = m;
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        A += __shfl_down_sync(0xffffffffu, A, off);
+        B += __shfl_down_sync(0xffffffffu, B, off);
+        C = __dadd_rn(C, __shfl_down_sync(0xffffffffu, C, off));
+        Dd = __dadd_rn(Dd, __shfl_down_sync(0xffffffffu, Dd, off));
+        F = __dadd_rn(F, __shfl_down_sync(0xffffffffu, F, off));
+        const long long lo = __shfl_down_sync(0xffffffffu, (long long)(unsigned long long)M, off);
+        const long long hi = __shfl_down_sync(0xffffffffu, (long long)(M >> 64), off);
+        const __int128 o = ((__int128)hi << 64) | (unsigned long long)lo;
+        if (o < M) M = o;
+    }
+    if (lane != 0) return;
     a.cur->sumE = A; a.cur->sumE2 = B;
     a.cur->sumEd = C; a.cur->sumE2d = Dd;
     a.cur->sum_clnc = F;
@@ -467,25 +674,26 @@ __device__ __forceinline__ void observe_final_body(const ObsArgs& a)
 }
 __global__ void observe_final_kernel(ObsArgs a)
 {
-    if (threadIdx.x == 0) observe_final_body(a);
+    if (threadIdx.x < 32) observe_final_body(a);
 }
+// one warp per instance
 __global__ void observe_final_batched(const ObsArgs* tab, int n_inst)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (i < n_inst) observe_final_body(tab[i]);
 }
 
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st)
 {
-    observe_partial_kernel<<<kObsBlocks, 1024, 0, st>>>(a);
+    observe_partial_kernel<<<obs_blocks(a.R), 1024, 0, st>>>(a);
     if (!a.sync) observe_final_kernel<<<1, 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, cudaStream_t st)
+cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, int maxR, cudaStream_t st)
 {
-    observe_partial_batched<<<dim3(kObsBlocks, (unsigned)n_inst), 1024, 0, st>>>(tab);
-    observe_final_batched<<<(n_inst + 63) / 64, 64, 0, st>>>(tab, n_inst);
+    observe_partial_batched<<<dim3(obs_blocks(maxR), (unsigned)n_inst), 1024, 0, st>>>(tab);
+    observe_final_batched<<<(n_inst + 7) / 8, 256, 0, st>>>(tab, n_inst);
     return cudaGetLastError();
 }
 
