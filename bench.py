@@ -18,8 +18,10 @@ clocks seen during the timed region and the kernel launch count.
 
 --impl reference times the CPU oracle (the plain C implementation that the
 parity tests compare against) on a bounded sample of the same workload.
-Multi-GPU (torchrun): one independent instance per rank, no collective on the
-data path; value = all ranks' attempts / max-over-ranks time (weak scaling).
+Multi-GPU (torchrun): disorder instances are the units, instance i on rank
+i mod N (its own couplings and Philox instance id), no collective on the data
+path; value = all ranks' attempts / max-over-ranks time (weak scaling); rank 0
+gathers every instance's last observables after the timed region.
 """
 from __future__ import annotations
 
@@ -218,6 +220,7 @@ def run_gpu(args, wl_name):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     P.load()
+    from paper_1710_09025_gb300 import dist as PD
     w = Wk.WORKLOADS[wl_name]
     J, h, betas = Wk.workload_inputs(wl_name)
     D, L, R, ns, kind = w["D"], w["L"], w["R"], w["n_sweeps"], w["kind"]
@@ -225,11 +228,17 @@ def run_gpu(args, wl_name):
         R = args.R
     N = L ** D
     betas = _schedule(betas, args.warmup + args.steps)
-    seed = w["seed"] + 1000 * rank
+    seed = w["seed"]
+    # disorder instances are the units across ranks: instance i (couplings of
+    # its own seed; instance 0 is the named workload) on rank i mod N, Philox
+    # instance id i
+    (inst,) = PD.partition(ws, rank, ws)
+    if inst > 0:
+        J, h = Wk.instance(D, L, kind, w["seed"] + inst)
     layout = {"packed": P.PA_LAYOUT_PACKED, "i8": P.PA_LAYOUT_I8}[w["layout"]]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        pop = P.Population(D, L, kind, J, h, R, betas, ns, seed, layout=layout)
+        pop = P.Population(D, L, kind, J, h, R, betas, ns, seed, layout=layout, rng_instance=inst)
     ctx = pop.ctx
     P.pa_profile(ctx, True)
     for _ in range(args.warmup):
@@ -260,6 +269,10 @@ def run_gpu(args, wl_name):
     value, ms = aggregate(e0.elapsed_time(e1), attempts_step, args.steps, ws, device="cuda")
     obs_last = P.pa_observables(ctx, args.warmup + args.steps - 1)
     pop.close()
+    # every instance's results at the last timed step, in instance order on rank 0
+    # (one collective after the timed region)
+    per_inst = PD.gather_rows(np.array([[obs_last["E_mean"] / N, obs_last["betaF"]]]), [inst], ws,
+                              device="cuda" if ws > 1 else "cpu")
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -285,7 +298,8 @@ def run_gpu(args, wl_name):
                    "schedule": "linear in beta, 0..%g" % w["beta_max"],
                    "timed_k": [args.warmup, args.warmup + args.steps - 1],
                    "l2": "state 2 x %.0f MB > 129 MB L2 (no flush needed)" % (8 * N * ((R + 63) // 64) / 1e6),
-                   "parallelism": "one independent instance per GPU"},
+                   "parallelism": "disorder instances partitioned across ranks: instance i on rank i mod N "
+                                  "(one per GPU), no collective in the timed region"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "sweep_packed_kernel" if w["layout"] == "packed" else "sweep_real_kernel",
@@ -310,6 +324,7 @@ def run_gpu(args, wl_name):
         "clocks": clocks,
         "observables_last": {"k": args.warmup + args.steps - 1, "E_mean_per_spin": obs_last["E_mean"] / N,
                              "betaF": obs_last["betaF"], "S_f": obs_last["S_f"]},
+        "instances": {"n": ws, "E_mean_per_spin": per_inst[:, 0].tolist(), "betaF": per_inst[:, 1].tolist()},
     }
     if not args.no_e2e and ws == 1:
         line["e2e"] = e2e_run(P, args, D, L, kind, J, h, R, betas, ns, seed, layout)
