@@ -544,6 +544,7 @@ static void fill_packed_step(pa::PackedStep* s, int D, double beta, int k, int n
     // dE, so classes never accepted are the large-dE ones)
     if (s->always == 0 && s->und == 2u) s->mode = 1;
     else if (s->always == 0 && s->und == 6u) s->mode = 2;
+    else if (D == 3 && s->always == 0 && s->und == 14u) s->mode = 3;  // every uphill class undecided
     else s->mode = 0;
     fill_round_keys(s->rk, k0, k1);
     // class of an uphill lane by its unsatisfied-bond count n: dE / 4 = D - n

@@ -68,8 +68,8 @@ bool batch_class(int D, int L, int kind, int mult, int G, int R, int* cls, int* 
         constexpr int g = default_shape<3, l>().gpb;                                          \
         *cls = 2 * idx;                                                                       \
         *tiles = (G + g * mult - 1) / (g * mult);                                             \
-        *smem = mult == 1 ? PackedShape<3, l, g, kBatchThreads>::SMEM                         \
-                          : PackedShape<3, l, 2 * g, kBatchThreads>::SMEM;                    \
+        *smem = mult == 1 ? PackedShape<3, l, g, kBatchThreads, false>::SMEM                  \
+                          : PackedShape<3, l, 2 * g, kBatchThreads, false>::SMEM;             \
         return true;                                                                          \
     }
         PA_BATCH_PACKED(XP)

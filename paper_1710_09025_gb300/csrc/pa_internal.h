@@ -24,7 +24,8 @@ static_assert(sizeof(StepAcc) == 96, "StepAcc layout");
 struct PackedStep {
     int k, n_sweeps;         // n_sweeps: sweeps of this launch
     uint32_t hs0;            // half-sweep index of its first half-sweep, 2 (k N_S + first sweep)
-    int mode;                // undecided uphill classes: 1 = {dE=4}, 2 = {dE=4, dE=8}, 0 = any set
+    int mode;                // undecided uphill classes: 1 = {dE=4}, 2 = {dE=4, dE=8},
+                             // 3 = every uphill class (3D, none always accepted), 0 = any set
     uint32_t und;            // bit c: class c (dE = 4c) needs a random comparison (0 < thr < 2^32)
     uint32_t always;         // bit c: class c always accepted (thr == 2^32)
     uint32_t rk[20];         // Philox round keys: rk[2r] = k0 + r W0, rk[2r+1] = k1 + r W1

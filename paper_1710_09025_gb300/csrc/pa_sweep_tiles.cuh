@@ -89,9 +89,12 @@ __device__ __forceinline__ void plane_step_two(uint64_t pl, uint32_t ta, uint32_
 // bits needed to count up to v
 __host__ __device__ constexpr int bits_for(int v) { return v <= 0 ? 1 : 1 + bits_for(v >> 1); }
 
-template <int D, int L, int GPB, int THREADS>
+// LATE: the late compaction of modes 0, 2 and 3 (single 3D instances with
+// L >= 8): its queue entries also carry the class bits of the undecided lanes
+template <int D, int L, int GPB, int THREADS, bool LATE = true>
 struct PackedShape {
     static constexpr int N = Lat<D, L>::N, NH = Lat<D, L>::NH;
+    static constexpr bool kLate = LATE && D == 3 && L >= 8;
     static constexpr int TPG = THREADS / GPB;         // threads per group in the energy phase
     static constexpr int SEGW = TPG < 32 ? TPG : 32;  // shuffle segment width
     static constexpr int NSEG = TPG / SEGW;           // segments (warps) per group
@@ -100,7 +103,10 @@ struct PackedShape {
     static constexpr size_t SJ = ((size_t)N + 15) / 16 * 16;
     static constexpr size_t CNT = (size_t)GPB * NSEG * B * 8;
     static constexpr int QIPT = 4;  // items per thread per queue round
-    static constexpr size_t QUEUE = 32 + (size_t)QIPT * THREADS * (8 + 4);  // queue of undecided words
+    static constexpr int QCAP = QIPT * THREADS;  // queue entries (every item of a round)
+    // queue of undecided words: counters, masks (two with the class bits), item indices
+    static constexpr size_t QUEUE = 32 + (size_t)QCAP * ((kLate ? 16 : 8) + 2);
+    static_assert(GPB * NH <= 65535, "item indices fit 16 bits");
     static constexpr size_t SMEM = TILE + SJ + CNT + QUEUE;
     static_assert(THREADS % GPB == 0 && (TPG & (TPG - 1)) == 0, "threads per group");
 };
@@ -129,7 +135,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                                                   unsigned char* smem)
 {
     using LT = Lat<D, L>;
-    using SH = PackedShape<D, L, GPB, THREADS>;
+    using SH = PackedShape<D, L, GPB, THREADS, LATE>;
     constexpr int N = SH::N, NH = SH::NH, TPG = SH::TPG, SEGW = SH::SEGW, NSEG = SH::NSEG, B = SH::B;
     constexpr int NWARP = THREADS / 32;
     uint64_t* sm = reinterpret_cast<uint64_t*>(smem);
@@ -216,8 +222,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     // item t = (group gl, sublattice index q) of parity p: neighbour decoding,
     // unsatisfied-bond counts n = b0 + 2 b1 + 4 b2 per lane, lanes with dE <= 0
     auto classify = [&](int t, int p, const typename LT::Nb& nb_fixed, uint64_t*& cur, int& q,
-                        uint64_t& sw0, uint64_t& b0, uint64_t& b1, uint64_t& b2, uint64_t& down,
-                        auto GEN) {
+                        uint64_t& sw0, uint64_t& b0, uint64_t& b1, uint64_t& b2, uint64_t& down) {
         const int gl = t / NH;
         q = t - gl * NH;
         cur = sm + (gl * 2 + p) * NH;
@@ -226,9 +231,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
         // when every item of this thread sits on the same sublattice site
         // (THREADS a multiple of N/2) decode once; when it sits on the same x-y
         // column (3D, THREADS a multiple of L^2/2) only z moves
-        if constexpr (decltype(GEN)::value) {
-            nb = LT::neighbours(p, q);
-        } else if constexpr (THREADS % NH == 0) {
+        if constexpr (THREADS % NH == 0) {
             nb = nb_fixed;
         } else if constexpr (D == 3 && THREADS % (LT::LH * L) == 0) {
             nb = LT::neighbours_column(p, q, xh_c, y_c);
@@ -327,8 +330,10 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     };
     // lanes that flip without a comparison (acc) and lanes that need one (U)
     auto start = [&](uint64_t b0, uint64_t b1, uint64_t b2, uint64_t down, uint64_t& acc, uint64_t& U) {
-        acc = down;  // in mode 2 no uphill class is always accepted
-        if (s.mode == 2) {
+        acc = down;  // in modes 2 and 3 no uphill class is always accepted
+        if (s.mode == 3) {
+            U = ~down;  // every uphill class undecided
+        } else if (s.mode == 2) {
             U = ~down & ((D == 3) ? (b0 | b1) : ~0ull);
         } else {
             uint64_t m1, m2, m3;
@@ -348,8 +353,9 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     // block queue: per round two counters (entries, next entry to take), then
     // the undecided masks and item indices
     int* qn = reinterpret_cast<int*>(qbuf);
-    uint64_t* QU = reinterpret_cast<uint64_t*>(qbuf + 32);
-    int* Qt = reinterpret_cast<int*>(QU + SH::QIPT * THREADS);
+    uint64_t* QU = reinterpret_cast<uint64_t*>(qbuf + 32);  // undecided lanes (late: class A)
+    uint64_t* QB = QU + SH::QCAP;                              // late: class B
+    uint16_t* Qt = reinterpret_cast<uint16_t*>(QU + (SH::kLate ? 2 : 1) * SH::QCAP);
     if (tid < 4) qn[tid] = 0;
     __syncthreads();
     int round = 0;
@@ -361,7 +367,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     // late compaction is measured faster for single 3D instances with L >= 8
     // (L=8: 2182 -> 2273 attempts/ns; L=16: 3108 -> 3197); the disorder batch
     // (L = 4..10, doubled groups per block) measured slower and keeps the loop
-    constexpr bool kLate = LATE && D == 3 && L >= 8;
+    constexpr bool kLate = SH::kLate;
 
     for (int sw = 0; sw < s.n_sweeps; ++sw) {
         for (int p = 0; p < 2; ++p) {
@@ -384,7 +390,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                             uint64_t* cur;
                             int q;
                             uint64_t sw0, b0, b1, b2, down;
-                            classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down, std::false_type{});
+                            classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
                             cur[q] = sw0 ^ down;  // no uphill class is always accepted in mode 1
                             U = ~down & ((D == 3) ? b1 : b0);
                         }
@@ -395,7 +401,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                         if (U) {
                             const int slot = wb + __popc(bal & ((1u << lane) - 1u));
                             QU[slot] = U;
-                            Qt[slot] = t;
+                            Qt[slot] = (uint16_t)t;
                         }
                     }
                     __syncthreads();
@@ -414,7 +420,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     uint64_t* cur;
                     int q;
                     uint64_t sw0, b0, b1, b2, down, acc, U;
-                    classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down, std::false_type{});
+                    classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
                     start(b0, b1, b2, down, acc, U);
                     compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
                                    std::integral_constant<int, 0>{}, std::integral_constant<int, 16>{});
@@ -423,23 +429,26 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                 __syncthreads();
             } else {
                 // Late compaction: every word gets its first KLATE Philox calls
-                // (8 planes) in place; a warp then waits for its slowest word only
-                // that far.  The ~12 % of words still undecided go to the block
-                // queue and finish there on full warps.  Same counters, so the
-                // same decisions (L=16: 3927 -> 3817 ms of sweeps per schedule;
-                // 3 calls: 4083 ms, 5 calls: 3937 ms)
-                constexpr int KLATE = 4;
+                // in place; a warp then waits for its slowest word only that
+                // far.  The words still undecided go to the block queue with
+                // the class bits of their undecided lanes (those lanes did not
+                // flip, so their classes are unchanged) and finish there on full
+                // warps, one word per thread, without classifying it again.
+                // Class code of an undecided lane: A = n <= 1, B = n >= 1
+                // (n = 0: A; n = 1: A and B; n = 2: B), so U = A | B,
+                // b0 = A & B, b1 = B & ~A.
+                constexpr int KLATE = 3;
                 for (int base = 0; base < ng * NH; base += SH::QIPT * THREADS, ++round) {
                     int* cnt_r = qn + 2 * (round & 1);
 #pragma unroll
                     for (int it = 0; it < SH::QIPT; ++it) {
                         const int t = base + it * THREADS + tid;
-                        uint64_t U = 0;
+                        uint64_t U = 0, b0 = 0, b1 = 0;
                         if (t < ng * NH) {
                             uint64_t* cur;
                             int q;
-                            uint64_t sw0, b0, b1, b2, down, acc;
-                            classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down, std::false_type{});
+                            uint64_t sw0, b2, down, acc;
+                            classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
                             start(b0, b1, b2, down, acc, U);
                             compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
                                            std::integral_constant<int, 0>{}, std::integral_constant<int, KLATE>{});
@@ -451,23 +460,21 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                         wb = __shfl_sync(0xffffffffu, wb, 0);
                         if (U) {
                             const int slot = wb + __popc(bal & ((1u << lane) - 1u));
-                            QU[slot] = U;
-                            Qt[slot] = t;
+                            QU[slot] = U & ~b1;         // A: n <= 1
+                            QB[slot] = U & (b0 | b1);   // B: n >= 1
+                            Qt[slot] = (uint16_t)t;
                         }
                     }
                     __syncthreads();
                     const int n = cnt_r[0];
                     if (tid == 0) { qn[2 * ((round + 1) & 1)] = 0; qn[2 * ((round + 1) & 1) + 1] = 0; }
                     for (int e = atomicAdd(cnt_r + 1, 1); e < n; e = atomicAdd(cnt_r + 1, 1)) {
-                        const int t2 = Qt[e];
-                        uint64_t* cur2;
-                        int q2;
-                        uint64_t sw1, b0, b1, b2, down, acc2 = 0, U2 = QU[e];
-                        // lanes still undecided were not flipped: their counts are unchanged
-                        classify(t2, p, nb_fixed, cur2, q2, sw1, b0, b1, b2, down, std::true_type{});
-                        compare_mode02((uint32_t)q2, (uint32_t)(g0 + t2 / NH), hs, U2, b0, b1, acc2,
+                        const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
+                        const uint64_t A = QU[e], Bm = QB[e];
+                        uint64_t U2 = A | Bm, acc2 = 0;
+                        compare_mode02((uint32_t)q2, (uint32_t)(g0 + gl2), hs, U2, A & Bm, Bm & ~A, acc2,
                                        std::integral_constant<int, KLATE>{}, std::integral_constant<int, 16>{});
-                        cur2[q2] = sw1 ^ acc2;
+                        sm[(gl2 * 2 + p) * NH + q2] ^= acc2;  // lanes accepted in the queue
                     }
                     __syncthreads();
                 }
