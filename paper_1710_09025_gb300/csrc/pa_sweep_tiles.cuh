@@ -430,14 +430,15 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
             } else {
                 // Late compaction: every word gets its first KLATE Philox calls
                 // in place; a warp then waits for its slowest word only that
-                // far.  The words still undecided go to the block queue with
+                // far (L=16, k=5..24: 3 calls 2552, 4 calls 2597, 5 calls 2328
+                // attempts/ns).  The words still undecided go to the block queue with
                 // the class bits of their undecided lanes (those lanes did not
                 // flip, so their classes are unchanged) and finish there on full
                 // warps, one word per thread, without classifying it again.
                 // Class code of an undecided lane: A = n <= 1, B = n >= 1
                 // (n = 0: A; n = 1: A and B; n = 2: B), so U = A | B,
                 // b0 = A & B, b1 = B & ~A.
-                constexpr int KLATE = 3;
+                constexpr int KLATE = 4;
                 for (int base = 0; base < ng * NH; base += SH::QIPT * THREADS, ++round) {
                     int* cnt_r = qn + 2 * (round & 1);
 #pragma unroll
