@@ -65,11 +65,11 @@ enum { PA_LAYOUT_AUTO = 0,   /* PM1 -> packed, REAL -> int8                     
 
 typedef struct {
     int32_t layout;          /* PA_LAYOUT_*                                            */
-    int32_t accumulate_grad; /* 1: keep per-temperature <s_i s_j>, <s_i> counts (REAL) */
+    int32_t accumulate_grad; /* 1: keep per-temperature <s_i s_j>, <s_i> population counts */
     uint32_t rng_instance;   /* 24-bit instance id in the Philox counter               */
     uint32_t rng_tag;        /* 4-bit tag: independent populations (overlap)           */
-    int32_t threads;         /* 0 = tuned default; else threads per block              */
-    int32_t groups_per_block;/* 0 = tuned default (packed layout)                      */
+    int32_t threads;         /* tile override: 0 = tuned default; else threads per block */
+    int32_t groups_per_block;/* tile override: 0 = tuned default (packed layout)       */
     /* dynamic population (Sec. III.D, Eq. 6): host array of n_temps replica
      * counts, populations[k] >= 1, the population R(beta_k) at temperature k
      * (exact for the multinomial scheme, the expectation for the
@@ -93,6 +93,11 @@ typedef struct {
      * of pa_check_accept_band; the decisions, and so every result, are the
      * same (0: the band where it is verified on the device) */
     int32_t exact_accept;
+    /* 1: the replica gather of a resampling step (slot j takes replica
+     * parent[j], Sec. II.B) runs as its own launch before the sweeps, which
+     * then work in place; 0: it is fused into the first sweep launch's tile
+     * load.  Same results either way.  Single contexts only. */
+    int32_t separate_gather;
 } pa_options;
 
 /* Per-temperature observables (Sec. II.B, Eq. 2-3; Sec. V.A, Eq. 9). */
@@ -114,7 +119,8 @@ int pa_options_default(pa_options* opt);
 
 /*
  * pa_create -- allocate a population of R replicas on the current CUDA device.
- *   D, L      lattice (D in {2,3}, L even, 2 <= L <= 16 in 3D, <= 64 in 2D)
+ *   D, L      lattice (D in {2,3}, L even; 3D: 2 <= L <= 16 for PA_PM1, <= 12 for
+ *             PA_REAL; 2D: L <= 64 for PA_PM1, <= 32 for PA_REAL)
  *   kind      PA_PM1 (J exactly +-1, h must be NULL or all zero) or PA_REAL
  *             (|J|,|h| < 4096; magnitudes below 2^-73 are flushed to zero so
  *             that energies are exact fixed-point integers at scale 2^-96)

@@ -43,7 +43,7 @@ class pa_options(ctypes.Structure):
                 ("populations", ctypes.c_void_p), ("resampling", ctypes.c_int32),
                 ("capacity", ctypes.c_int32), ("icm", ctypes.c_int32),
                 ("icm_beta_lo", ctypes.c_double), ("icm_beta_hi", ctypes.c_double),
-                ("exact_accept", ctypes.c_int32)]
+                ("exact_accept", ctypes.c_int32), ("separate_gather", ctypes.c_int32)]
 
 
 class pa_inst_desc(ctypes.Structure):

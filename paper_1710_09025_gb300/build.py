@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpamc.so")
 SOURCES = ["pa_packed_part0.cu", "pa_packed_part1.cu", "pa_packed_part2.cu", "pa_packed_part3.cu",
            "pa_batch.cu", "pa_real.cu", "pa_api.cu", "pa_packed.cu", "pa_resample.cu", "pa_noalloc.cu",
-           "pa_icm.cu"]
+           "pa_icm.cu", "pa_gather_grad.cu"]
 HEADERS = ["pa_device.cuh", "pa_internal.h", "pa_sweep_tiles.cuh", "pa_packed_sweep.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",

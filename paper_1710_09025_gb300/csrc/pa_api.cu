@@ -27,6 +27,7 @@ struct pa_ctx {
     uint64_t seed;
     uint32_t inst, tag;
     int acc_grad;
+    int sep_gather;             // the replica gather as its own launch before the sweeps
     cudaStream_t st;
     int gpb, threads, real_warps;
     int band;                   // real couplings: acceptance guard band verified on this device
@@ -239,7 +240,7 @@ static int validate(std::string& err, int D, int L, int kind, const float* J, co
     if (lay != PA_LAYOUT_PACKED && lay != PA_LAYOUT_I8) { err = "unknown layout"; return PA_EINVAL; }
     if (lay == PA_LAYOUT_PACKED && kind != PA_PM1) { err = "packed layout needs +-J couplings"; return PA_EINVAL; }
     bool sup = (kind == PA_PM1) ? pa::packed_supported(D, L) : pa::real_supported(D, L);
-    if (!sup) { err = "lattice size not compiled in (3D: L in 2..12 even or 16; 2D: up to 32/64)"; return PA_EINVAL; }
+    if (!sup) { err = "lattice size not compiled in (3D: even L in 2..16, real couplings 2..12; 2D: up to 32/64)"; return PA_EINVAL; }
     if (R < 1 || R > (1 << 26)) { err = "R must be in [1, 2^26]"; return PA_EINVAL; }
     if (n_temps < 1 || !betas) { err = "need at least one temperature"; return PA_EINVAL; }
     if (betas[0] != 0.0) { err = "betas[0] must be 0 (beta F starts from -N ln 2)"; return PA_EINVAL; }
@@ -263,7 +264,6 @@ static int validate(std::string& err, int D, int L, int kind, const float* J, co
         }
     }
     if (o) {
-        if (o->accumulate_grad && kind != PA_REAL) { err = "accumulate_grad needs PA_REAL"; return PA_EINVAL; }
         if (o->rng_instance >= (1u << 24)) { err = "rng_instance must be < 2^24"; return PA_EINVAL; }
         if (o->rng_tag >= 16u) { err = "rng_tag must be < 16"; return PA_EINVAL; }
         if (o->resampling != PA_RESAMPLE_MULTINOMIAL && o->resampling != PA_RESAMPLE_NEAREST) {
@@ -347,6 +347,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->icm = o.icm ? 1 : 0; c->icm_lo = o.icm_beta_lo; c->icm_hi = o.icm_beta_hi; c->n_temps = n_temps; c->n_sweeps = n_sweeps; c->k_next = 0;
     c->layout = resolve_layout(kind, &o); c->NP = (c->N + 15) / 16 * 16;
     c->seed = seed; c->inst = o.rng_instance; c->tag = o.rng_tag; c->acc_grad = o.accumulate_grad ? 1 : 0;
+    c->sep_gather = o.separate_gather ? 1 : 0;
     c->st = (cudaStream_t)stream;
     c->betas.assign(betas, betas + n_temps);
     c->Rk.assign(n_temps, R);
@@ -575,6 +576,14 @@ struct StepPlan {
     pa::PackedSweepArgs pk2;
     pa::RealSweepArgs re2;
     pa::ObsArgs ob;
+    // separate_gather (k > 0): the gather launch, then the sweeps in place
+    bool gather;
+    const uint64_t* g_Sin;
+    uint64_t* g_Sout;
+    const int8_t* g_S8in;
+    int8_t* g_S8out;
+    // +-J gradient counts of the population after the sweeps
+    bool grad_pm;
     // context state after the step
     int cur, famcur;
 };
@@ -684,6 +693,28 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         ic.err = c->icm_err;
         if (c->layout != PA_LAYOUT_PACKED || c->kind == PA_REAL) c->cur ^= 1;  // the second sweep launch ping-pongs
     }
+    if (c->sep_gather && k > 0) {
+        // the gather the first sweep launch would fuse runs as its own launch
+        // into the buffer that launch writes; that launch then sweeps in place
+        pl->gather = true;
+        if (c->kind == PA_PM1) {
+            pa::PackedInst& in = pl->pk.i;
+            if (c->layout == PA_LAYOUT_PACKED) {
+                pl->g_Sin = in.Sin; pl->g_Sout = in.S;
+                in.Sin = in.S;
+            } else {
+                pl->g_S8in = in.S8_in; pl->g_S8out = in.S8_out;
+                in.S8_in = in.S8_out;
+            }
+            in.parent = nullptr;
+        } else {
+            pa::RealInst& in = pl->re.i;
+            pl->g_S8in = in.Sin; pl->g_S8out = in.Sout;
+            in.Sin = in.Sout;
+            in.parent = nullptr;
+        }
+    }
+    pl->grad_pm = c->acc_grad && c->kind == PA_PM1;
     pa::ObsArgs& oa = pl->ob;
     oa.R = R; oa.kind = c->kind == PA_PM1 ? 0 : 1; oa.E32 = c->E32; oa.E128 = c->E128;
     if (dyn) { oa.Rdev = c->Rdev + k; oa.R = c->R; }
@@ -731,6 +762,14 @@ static int enqueue_step(pa_ctx* c)
         c->launches += pl.rs.wtab ? 6 : 5;
         phase_end(c, PA_PHASE_RESAMPLE, ev);
     }
+    if (pl.gather) {
+        ev = phase_begin(c, PA_PHASE_GATHER);
+        const bool dyn = c->scheme == PA_RESAMPLE_NEAREST;
+        PA_CK(c, pa::launch_gather(pl.g_Sin, pl.g_Sout, pl.g_S8in, pl.g_S8out, c->parent, c->N, c->NP,
+                                   dyn ? c->R : c->Rk[k], dyn ? c->Rdev + k : nullptr, c->st));
+        c->launches += 1;
+        phase_end(c, PA_PHASE_GATHER, ev);
+    }
     ev = phase_begin(c, PA_PHASE_SWEEP);
     if (c->kind == PA_PM1)
         PA_CK(c, pa::launch_sweep_packed(c->D, c->L, pl.pk, c->gpb, c->threads, c->st));
@@ -748,6 +787,15 @@ static int enqueue_step(pa_ctx* c)
         else
             PA_CK(c, pa::launch_sweep_real(c->D, c->L, pl.re2, c->real_warps, 0, c->st));
         c->launches += 3;
+    }
+    if (pl.grad_pm) {
+        const bool dyn = c->scheme == PA_RESAMPLE_NEAREST;
+        const bool packed = c->layout == PA_LAYOUT_PACKED;
+        PA_CK(c, pa::launch_grad_counts_pm(packed ? c->S[pl.cur] : nullptr, packed ? nullptr : c->S8[pl.cur],
+                                           c->NP, c->D, c->L, dyn ? c->R : c->Rk[k],
+                                           dyn ? c->Rdev + k : nullptr, c->cJ + (size_t)k * c->D * c->N,
+                                           c->ch + (size_t)k * c->N, c->st));
+        c->launches += 1;
     }
     phase_end(c, PA_PHASE_SWEEP, ev);
     ev = phase_begin(c, PA_PHASE_OBSERVE);
@@ -1270,7 +1318,7 @@ extern "C" int pa_batch_create(pa_batch** out, int D, int n_inst, const pa_inst_
     *out = nullptr;
     if (D != 3) { g_create_err = "batched sweeps support D = 3"; return PA_EINVAL; }
     if (n_inst < 1 || !descs) { g_create_err = "need at least one instance"; return PA_EINVAL; }
-    if (opt && (opt->layout != PA_LAYOUT_AUTO || opt->accumulate_grad || opt->populations ||
+    if (opt && (opt->layout != PA_LAYOUT_AUTO || opt->accumulate_grad || opt->populations || opt->separate_gather ||
                 opt->resampling != PA_RESAMPLE_MULTINOMIAL || opt->capacity || opt->icm)) {
         g_create_err = "batch: layout must be AUTO, accumulate_grad 0, populations NULL, multinomial "
                        "resampling and no capacity";

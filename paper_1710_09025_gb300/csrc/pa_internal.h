@@ -63,6 +63,16 @@ cudaError_t launch_unpack_packed(const uint64_t* S, int8_t* out, int N, int r0, 
 cudaError_t launch_overlap_packed(const uint64_t* A, const uint64_t* B, int N, int R,
                                   unsigned long long* hist, cudaStream_t st);
 
+// the replica gather as its own launch (packed words if Sin, else int8 rows):
+// slot j of the new population takes replica parent[j]
+cudaError_t launch_gather(const uint64_t* Sin, uint64_t* Sout, const int8_t* S8in, int8_t* S8out,
+                          const int32_t* parent, int N, int NP, int R, const int* Rdev, cudaStream_t st);
+// gradient counts of a +-J population after the sweeps (packed words if S,
+// else int8 rows), added to cJ (D*N) and ch (N) of this step
+cudaError_t launch_grad_counts_pm(const uint64_t* S, const int8_t* S8, int NP, int D, int L, int R,
+                                  const int* Rdev, unsigned long long* cJ, unsigned long long* ch,
+                                  cudaStream_t st);
+
 // ---------------- int8 path ----------------
 struct RealStep {
     int k, n_sweeps;         // n_sweeps: sweeps of this launch

@@ -28,7 +28,7 @@ namespace pa {
 // ---------------- shapes and dispatch ----------------
 
 #define PA_PACKED_CASES(X) \
-    X(3, 2) X(3, 4) X(3, 6) X(3, 8) X(3, 10) X(3, 12) X(3, 16) \
+    X(3, 2) X(3, 4) X(3, 6) X(3, 8) X(3, 10) X(3, 12) X(3, 14) X(3, 16) \
     X(2, 2) X(2, 4) X(2, 6) X(2, 8) X(2, 10) X(2, 12) X(2, 16) X(2, 32) X(2, 64)
 
 bool packed_supported(int D, int L)

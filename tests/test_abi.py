@@ -69,9 +69,9 @@ def test_validation_rejects(lib, kw, needle):
 def test_option_validation(lib):
     import paper_1710_09025_gb300 as P
     P.load(lib._name)
-    o = P.pa_options_default(accumulate_grad=1)
+    o = P.pa_options_default(accumulate_grad=1, separate_gather=1)
     rc, out, msg = _create(lib, kind=0, opt=o)
-    assert rc == -1 and "PA_REAL" in msg
+    assert rc != -1  # valid for +-J couplings too (no GPU here: the allocation fails instead)
     o = P.pa_options_default(rng_tag=16)
     rc, out, msg = _create(lib, opt=o)
     assert rc == -1 and "rng_tag" in msg
@@ -147,4 +147,4 @@ def test_packed_sweep_parts_cover_every_lattice_once():
         body = src[src.index("#define X(d, l)"):src.index("#undef X")]
         parts += re.findall(r"X\((\d), (\d+)\)", body.split("\n", 1)[1])
     assert len(parts) == len(set(parts))
-    assert sorted(parts) == sorted(supported) and len(supported) == 16
+    assert sorted(parts) == sorted(supported) and len(supported) == 17

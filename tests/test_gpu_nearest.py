@@ -17,12 +17,13 @@ PM1, REAL = 0, 1
 
 
 def _run(pa, oracle, D, L, kind, J, h, R, betas, ns, seed, layout=0, populations=None, capacity=0,
-         grad=False, graph=False):
+         grad=False, graph=False, **extra):
     P = pa
     ref = oracle.Sim(D, L, kind, J, h, R, betas, ns, seed, populations=populations, resampling=1,
                      capacity=capacity, accumulate_grad=grad)
     pop = P.Population(D, L, kind, J, h, R, betas, ns, seed, layout=layout, populations=populations,
-                       resampling=P.PA_RESAMPLE_NEAREST, capacity=capacity, accumulate_grad=int(grad))
+                       resampling=P.PA_RESAMPLE_NEAREST, capacity=capacity, accumulate_grad=int(grad),
+                       **extra)
     try:
         if graph:
             pop.run(graph=True)

@@ -33,7 +33,7 @@ def _assert_obs(o, r, kind):
 
 
 def run_parity(pa, oracle, D, L, kind, J, h, R, betas, ns, seed, layout=0, inst=0, tag=0,
-               grad=False, graph_every=None, shape=None, populations=None):
+               grad=False, graph_every=None, shape=None, populations=None, **extra):
     P = pa
     ref = oracle.Sim(D, L, kind, J, h, R, betas, ns, seed, rng_instance=inst, rng_tag=tag,
                      accumulate_grad=grad, populations=populations)
@@ -41,6 +41,7 @@ def run_parity(pa, oracle, D, L, kind, J, h, R, betas, ns, seed, layout=0, inst=
                 populations=populations)
     if shape:
         opts.update(groups_per_block=shape[0], threads=shape[1])
+    opts.update(extra)
     pop = P.Population(D, L, kind, J, h, R, betas, ns, seed, **opts)
     try:
         for k in range(len(betas)):
@@ -72,7 +73,7 @@ def run_parity(pa, oracle, D, L, kind, J, h, R, betas, ns, seed, layout=0, inst=
 
 @pytest.mark.parametrize("D,L,R,nt,ns", [
     (3, 4, 200, 9, 4), (3, 6, 130, 7, 3), (3, 8, 65, 6, 2), (3, 10, 193, 4, 2), (3, 12, 20, 3, 2),
-    (3, 16, 70, 3, 2), (3, 2, 70, 8, 5), (2, 6, 100, 8, 4), (2, 4, 64, 8, 3), (2, 8, 257, 6, 3),
+    (3, 16, 70, 3, 2), (3, 14, 90, 3, 2), (3, 2, 70, 8, 5), (2, 6, 100, 8, 4), (2, 4, 64, 8, 3), (2, 8, 257, 6, 3),
     (2, 2, 9, 5, 3), (2, 16, 33, 4, 2), (2, 32, 64, 3, 2), (2, 64, 10, 2, 1),
 ])
 def test_packed_pm_parity(pa, oracle, D, L, R, nt, ns):
