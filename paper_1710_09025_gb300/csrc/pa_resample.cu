@@ -54,11 +54,13 @@ __device__ __forceinline__ bool last_block(int* counter)
 // source population: in device memory for the nearest-integer scheme
 __device__ __forceinline__ int rs_src(const ResampleArgs& a) { return a.Rsrc ? *a.Rsrc : a.R; }
 
-// Weights and the two lowest levels of the prefix, one block of kWBlock
-// threads per kWBlock weights.  GB300 has little FP64 throughput, so every
+// Weights and the two lowest levels of the prefix, one block of kWThreads
+// threads per kWBlock weights (small blocks, so that several blocks' FP64
+// chains overlap on an SM).  GB300 has little FP64 throughput, so every
 // addition of the specified order is executed once: lane c of warp 0 sums
-// run c (32 weights, staged in shared memory) left to right, then lane 0
-// sums the block's run totals left to right.
+// run c (32 weights, staged in shared memory, loaded eight at a time) left
+// to right, then lane 0 sums the block's run totals left to right.
+constexpr int kWThreads = 256;
 __device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int b)
 {
     __shared__ double s_w[kFan * (kFan + 1)];  // run c at [c (kFan + 1)], padded against bank conflicts
@@ -68,8 +70,8 @@ __device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int b)
     if (i0 >= R) return;  // block-uniform: past the source population
     const int tid = threadIdx.x;
     const int n = min(kWBlock, R - i0);
-    const int i = i0 + tid;
-    if (tid < n) {
+    for (int t = tid; t < n; t += kWThreads) {
+        const int i = i0 + t;
         double w;
         const int lv = a.kind == 0 ? a.E32[i] - (int)a.prev->emin_lo : 0;
         if (a.wtab && (lv & 3) == 0 && (lv >> 2) < a.wtab_n) {
@@ -79,22 +81,30 @@ __device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int b)
             w = spec_exp64(-__dmul_rn(a.dbeta, d));
         }
         a.w[i] = w;
-        s_w[(tid / kFan) * (kFan + 1) + tid % kFan] = w;
+        s_w[(t / kFan) * (kFan + 1) + t % kFan] = w;
     }
     __syncthreads();
     const int nruns = (n + kFan - 1) / kFan;
     if (tid < nruns) {  // run tid, left to right
         double* x = s_w + tid * (kFan + 1);
         const int cnt = min(kFan, n - tid * kFan);
-        double acc = x[0];
-        for (int j = 1; j < cnt; ++j) {
-            acc = __dadd_rn(acc, x[j]);
-            x[j] = acc;
+        double acc = 0.0;
+        for (int j0 = 0; j0 < cnt; j0 += 8) {
+            double v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = j0 + j < cnt ? x[j0 + j] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j0 + j < cnt) {
+                    acc = (j0 + j == 0) ? v[0] : __dadd_rn(acc, v[j]);
+                    x[j0 + j] = acc;
+                }
+            }
         }
         s_t[tid] = acc;
     }
     __syncthreads();
-    if (tid < n) a.P[i] = s_w[(tid / kFan) * (kFan + 1) + tid % kFan];
+    for (int t = tid; t < n; t += kWThreads) a.P[i0 + t] = s_w[(t / kFan) * (kFan + 1) + t % kFan];
     if (tid == 0) {  // the block's run totals, left to right
         double acc = s_t[0];
         a.lev1[b * kFan] = acc;
@@ -106,12 +116,12 @@ __device__ __forceinline__ void rs_weights_body(const ResampleArgs& a, int b)
     }
 }
 __device__ __forceinline__ void rs_top_body(const ResampleArgs& a);
-__global__ void __launch_bounds__(kWBlock) rs_weights_kernel(ResampleArgs a)
+__global__ void __launch_bounds__(kWThreads) rs_weights_kernel(ResampleArgs a)
 {
     rs_weights_body(a, blockIdx.x);
     if (a.sync && last_block(a.sync)) rs_top_body(a);  // levels >= 2 of the prefix
 }
-__global__ void __launch_bounds__(kWBlock) rs_weights_batched(const ResampleArgs* tab)
+__global__ void __launch_bounds__(kWThreads) rs_weights_batched(const ResampleArgs* tab)
 {
     const ResampleArgs& a = tab[blockIdx.y];
     rs_weights_body(a, blockIdx.x);
@@ -188,8 +198,9 @@ __device__ __forceinline__ long long dbits(double x) { return __double_as_longlo
 // these up to i within the block; bmax[b] = the block's largest.
 __device__ __forceinline__ void rs_finalize_body(const ResampleArgs& a, int b)
 {
+    constexpr int PER = kWBlock / kWThreads;  // consecutive weights per thread
     __shared__ double s_q[kFan];
-    __shared__ long long s_m[32];
+    __shared__ long long s_m[kWThreads / 32];
     const int R = rs_src(a);
     const int i0 = b * kWBlock;
     if (i0 >= R) return;  // block-uniform
@@ -205,32 +216,45 @@ __device__ __forceinline__ void rs_finalize_body(const ResampleArgs& a, int b)
         s_q[tid] = q;
     }
     __syncthreads();
-    const int i = i0 + tid;
+    long long v[PER];
     long long m = 0;  // bits of +0.0: weights are >= 0
-    if (i < R) {
-        const double l = a.P[i];
-        m = dbits(i < kFan ? l : __dadd_rn(s_q[tid / kFan], l));
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int i = i0 + tid * PER + j;
+        long long x = 0;
+        if (i < R) {
+            const double l = a.P[i];
+            x = dbits(i < kFan ? l : __dadd_rn(s_q[(tid * PER + j) / kFan], l));
+        }
+        m = max(m, x);
+        v[j] = m;  // inclusive maximum within this thread's weights
     }
+    long long incl = m;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const long long v = __shfl_up_sync(0xffffffffu, m, o);
-        if (lane >= o) m = max(m, v);
+        const long long u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl = max(incl, u);
     }
-    if (lane == 31) s_m[warp] = m;
+    if (lane == 31) s_m[warp] = incl;
+    const long long up = __shfl_up_sync(0xffffffffu, incl, 1);
     __syncthreads();
-    long long before = 0;
-    for (int v = 0; v < warp; ++v) before = max(before, s_m[v]);
-    if (i < R) a.P[i] = __longlong_as_double(max(before, m));
+    long long before = lane > 0 ? up : 0;
+    for (int w = 0; w < warp; ++w) before = max(before, s_m[w]);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int i = i0 + tid * PER + j;
+        if (i < R) a.P[i] = __longlong_as_double(max(before, v[j]));
+    }
     if (tid == 0) {
         long long bm = 0;
-        for (int v = 0; v < 32; ++v) bm = max(bm, s_m[v]);
+        for (int w = 0; w < kWThreads / 32; ++w) bm = max(bm, s_m[w]);
         a.bmax[b] = __longlong_as_double(bm);
     }
 }
 // running maximum over the weights blocks (bmax[nb + b] = the largest
 // cumulative weight before block b), S = the largest cumulative weight, ln Q
-// and the running free energy; one block of kWBlock threads, kWBlock block
-// maxima per pass (integer maxima of the bit patterns)
+// and the running free energy; one block, as many block maxima per pass as it
+// has threads (integer maxima of the bit patterns)
 __device__ __forceinline__ void rs_blockmax_body(const ResampleArgs& a)
 {
     __shared__ long long s_w[32];
@@ -240,7 +264,8 @@ __device__ __forceinline__ void rs_blockmax_body(const ResampleArgs& a)
     const int nb = rs_wblocks(R);
     if (tid == 0) s_carry = 0;
     __syncthreads();
-    for (int b0 = 0; b0 < nb; b0 += kWBlock) {
+    const int nt = blockDim.x;
+    for (int b0 = 0; b0 < nb; b0 += nt) {
         const int b = b0 + tid;
         long long m = b < nb ? dbits(a.bmax[b]) : 0;
 #pragma unroll
@@ -256,7 +281,7 @@ __device__ __forceinline__ void rs_blockmax_body(const ResampleArgs& a)
         const long long up = __shfl_up_sync(0xffffffffu, m, 1);
         const long long excl = lane > 0 ? max(before, up) : before;
         if (b < nb) a.bmax[nb + b] = __longlong_as_double(excl);
-        if (tid == kWBlock - 1) s_carry = max(before, m);
+        if (tid == nt - 1) s_carry = max(before, m);
         __syncthreads();
     }
     if (tid != 0) return;
@@ -276,12 +301,12 @@ __device__ __forceinline__ void rs_blockmax_body(const ResampleArgs& a)
     a.cur->betaF = __dsub_rn(a.betaF0, sum);
     a.cur->S = S;
 }
-__global__ void __launch_bounds__(kWBlock) rs_finalize_kernel(ResampleArgs a)
+__global__ void __launch_bounds__(kWThreads) rs_finalize_kernel(ResampleArgs a)
 {
     rs_finalize_body(a, blockIdx.x);
     if (a.sync && last_block(a.sync + 3)) rs_blockmax_body(a);
 }
-__global__ void __launch_bounds__(kWBlock) rs_finalize_batched(const ResampleArgs* tab)
+__global__ void __launch_bounds__(kWThreads) rs_finalize_batched(const ResampleArgs* tab)
 {
     rs_finalize_body(tab[blockIdx.y], blockIdx.x);
 }
@@ -502,9 +527,9 @@ cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
 {
     const int nb = (a.R + kScanBlock - 1) / kScanBlock;
     if (a.wtab) rs_table_kernel<<<(a.wtab_n + 255) / 256, 256, 0, st>>>(a);
-    rs_weights_kernel<<<rs_wblocks(a.R), kWBlock, 0, st>>>(a);
+    rs_weights_kernel<<<rs_wblocks(a.R), kWThreads, 0, st>>>(a);
     if (!a.sync) rs_top_kernel<<<1, kWBlock, 0, st>>>(a);
-    rs_finalize_kernel<<<rs_wblocks(a.R), kWBlock, 0, st>>>(a);
+    rs_finalize_kernel<<<rs_wblocks(a.R), kWThreads, 0, st>>>(a);
     if (!a.sync) rs_blockmax_kernel<<<1, kWBlock, 0, st>>>(a);
     if (a.scheme == 1)
         rs_nearest_kernel<<<(a.R + 255) / 256, 256, 0, st>>>(a);
@@ -520,9 +545,9 @@ cudaError_t launch_resample_batched(const ResampleArgs* tab, int n_inst, int max
 {
     const unsigned nb = (maxR + kScanBlock - 1) / kScanBlock;
     const unsigned ni = (unsigned)n_inst;
-    rs_weights_batched<<<dim3(rs_wblocks(maxR), ni), kWBlock, 0, st>>>(tab);
+    rs_weights_batched<<<dim3(rs_wblocks(maxR), ni), kWThreads, 0, st>>>(tab);
     rs_top_batched<<<ni, kWBlock, 0, st>>>(tab, n_inst);
-    rs_finalize_batched<<<dim3(rs_wblocks(maxR), ni), kWBlock, 0, st>>>(tab);
+    rs_finalize_batched<<<dim3(rs_wblocks(maxR), ni), kWThreads, 0, st>>>(tab);
     rs_blockmax_batched<<<ni, kWBlock, 0, st>>>(tab, n_inst);
     rs_draws_batched<<<dim3((maxR + kDrawThreads - 1) / kDrawThreads, ni), kDrawThreads, 0, st>>>(tab);
     rs_blocksum_batched<<<dim3(nb, ni), 1024, 0, st>>>(tab);
