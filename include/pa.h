@@ -98,6 +98,14 @@ typedef struct {
      * then work in place; 0: it is fused into the first sweep launch's tile
      * load.  Same results either way.  Single contexts only. */
     int32_t separate_gather;
+    /* a shard of one population spread over several contexts (one per GPU;
+     * Sec. V.A: replicas numbered globally, every rank holding an equal share):
+     * the context holds the global replicas [shard_offset, shard_offset + R)
+     * of shard_total (shard_offset a multiple of 1024; +-J couplings, packed
+     * layout, fixed population, multinomial resampling).  Step 0 runs with
+     * pa_anneal_step; later steps with the pa_shard_* phases below.
+     * shard_total = 0: not a shard. */
+    int32_t shard_offset, shard_total;
 } pa_options;
 
 /* Per-temperature observables (Sec. II.B, Eq. 2-3; Sec. V.A, Eq. 9). */
@@ -271,6 +279,57 @@ int pa_batch_instance(pa_batch* b, int i, pa_ctx** out);
 int pa_batch_sweep_config(const pa_batch* b, int* blocks, int* gpb_mult, double* ms);
 const char* pa_batch_last_error(const pa_batch* b);  /* NULL: last pa_batch_create failure */
 void pa_batch_destroy(pa_batch* b);
+
+/* ---------------- shards of one population (Sec. V.A) ----------------
+ * One population of shard_total replicas split over several contexts, one per
+ * GPU, each holding the replicas [shard_offset, shard_offset + R) (the
+ * paper's global replica numbering); after every resampling each shard again
+ * holds its own range of slots (equal shares, the paper's load balancing).
+ * Random streams follow the global replica numbers, and the summation order
+ * of the weights is that of one context, so a sharded run gives bit for bit
+ * the results of one context of shard_total replicas (spins, energies,
+ * parents, families, ln Q, beta F).  Step 0 runs with pa_anneal_step; a step
+ * k >= 1 runs these phases in order, the caller exchanging between them (in
+ * shard order): every phase synchronises the context's stream.
+ *   1. pa_shard_emin: this shard's lowest energy after step k-1 (the caller
+ *      takes the minimum over the shards).
+ *   2. pa_shard_weights(E_min of all shards): resampling weights and the two
+ *      lowest summation levels of the local weights blocks; writes the
+ *      rs = ceil(R / 1024) local block totals (host doubles).
+ *   3. pa_shard_prefix(all shards' block totals, ceil(shard_total / 1024),
+ *      concatenated in shard order): the higher levels (identical on every
+ *      shard) and the local cumulative weights; writes the rs local block
+ *      maxima.
+ *   4. pa_shard_draw(all shards' block maxima): S, ln Q and beta F of step k
+ *      (the same on every shard), then the shard_total draws, of which the
+ *      local ones are counted; *copies = the copies of local replicas.
+ *   5. pa_shard_copies: the global parent index and family of every local
+ *      copy (host int32 [copies] each), in slot order.  The copies of shard s
+ *      take the global slots [sum_{t<s} copies_t, ...).  The caller sends each
+ *      slot's parent, family and replica to the shard owning the slot.
+ *   6. pa_shard_pack(replicas, n, dst): the spins of n increasing global
+ *      replica indices of this shard packed into ceil(n/64) groups of N
+ *      uint64 words (replica i at bit i % 64 of group i / 64) at dst (host,
+ *      or device memory of this GPU when dst_on_device).
+ *   7. pa_shard_finish(groups, n_groups, parent, family): the incoming
+ *      replica groups (at most ceil(R/64) + 64), and for each of the R local
+ *      slots the index of its parent among them and its family; then the N_S
+ *      sweeps of step k (the gather reading the incoming replicas) and the
+ *      local observables.
+ * pa_shard_sums(k): the exact local sum of E and E^2 after step k and the
+ * local lowest energy (the caller adds the shards' sums for <E>, <E^2>).
+ * pa_observables on a shard gives the global ln Q and beta F and the local
+ * averages.  Errors: PA_EINVAL, PA_ESTATE (not a shard, or no step to run),
+ * PA_ECUDA. */
+int pa_shard_emin(pa_ctx* ctx, int64_t* emin);
+int pa_shard_weights(pa_ctx* ctx, int64_t emin_global, double* host_block_totals);
+int pa_shard_prefix(pa_ctx* ctx, const double* host_all_totals, double* host_block_max);
+int pa_shard_draw(pa_ctx* ctx, const double* host_all_block_max, int32_t* copies);
+int pa_shard_copies(pa_ctx* ctx, int32_t* host_parent, int32_t* host_family);
+int pa_shard_pack(pa_ctx* ctx, const int32_t* host_replicas, int n, void* dst, int dst_on_device);
+int pa_shard_finish(pa_ctx* ctx, const void* groups, int n_groups, int src_on_device,
+                    const int32_t* host_parent, const int32_t* host_family);
+int pa_shard_sums(pa_ctx* ctx, int k, int64_t* sums /* 3: sum E, sum E^2, lowest E */);
 
 /*
  * pa_resample_static -- the resampling step of pa_anneal_step for a +-J

@@ -43,7 +43,8 @@ class pa_options(ctypes.Structure):
                 ("populations", ctypes.c_void_p), ("resampling", ctypes.c_int32),
                 ("capacity", ctypes.c_int32), ("icm", ctypes.c_int32),
                 ("icm_beta_lo", ctypes.c_double), ("icm_beta_hi", ctypes.c_double),
-                ("exact_accept", ctypes.c_int32), ("separate_gather", ctypes.c_int32)]
+                ("exact_accept", ctypes.c_int32), ("separate_gather", ctypes.c_int32),
+                ("shard_offset", ctypes.c_int32), ("shard_total", ctypes.c_int32)]
 
 
 class pa_inst_desc(ctypes.Structure):
@@ -99,6 +100,14 @@ def load(path: str | None = None):
             "pa_checkpoint_load": (i32, [vp, vp, sz]),
             "pa_profile": (i32, [vp, i32]),
             "pa_phase_times": (i32, [vp, vp, vp, vp]),
+            "pa_shard_emin": (i32, [vp, P(i64)]),
+            "pa_shard_weights": (i32, [vp, i64, vp]),
+            "pa_shard_prefix": (i32, [vp, vp, vp]),
+            "pa_shard_draw": (i32, [vp, vp, P(ctypes.c_int32)]),
+            "pa_shard_copies": (i32, [vp, vp, vp]),
+            "pa_shard_pack": (i32, [vp, vp, i32, vp, i32]),
+            "pa_shard_finish": (i32, [vp, vp, i32, i32, vp, vp]),
+            "pa_shard_sums": (i32, [vp, i32, vp]),
             "pa_resample_static": (i32, [vp, i32, ctypes.c_double, ctypes.c_double, i32, u64,
                                          ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp]),
             "pa_batch_create": (i32, [P(vp), i32, i32, vp, vp, i32, i32, u64, P(pa_options), vp]),
@@ -342,6 +351,69 @@ def pa_resample_static(d_E, R, beta_prev, beta_next, k, seed, rng_instance, rng_
     _check(load().pa_resample_static(ctypes.c_void_p(d_E), R, beta_prev, beta_next, k, seed,
                                      rng_instance, rng_tag, ctypes.c_void_p(d_parent),
                                      ctypes.c_void_p(d_lnQ), st))
+
+
+# ---------------- shards of one population ----------------
+
+def pa_shard_emin(ctx) -> int:
+    v = ctypes.c_int64(0)
+    _check(load().pa_shard_emin(ctx, ctypes.byref(v)), ctx)
+    return int(v.value)
+
+
+def pa_shard_weights(ctx, emin_global) -> np.ndarray:
+    R = pa_sizes(ctx)["R"]
+    out = np.empty((R + 1023) // 1024)
+    _check(load().pa_shard_weights(ctx, int(emin_global), _ptr(out)), ctx)
+    return out
+
+
+def pa_shard_prefix(ctx, all_totals) -> np.ndarray:
+    R = pa_sizes(ctx)["R"]
+    t = np.ascontiguousarray(all_totals, dtype=np.float64)
+    out = np.empty((R + 1023) // 1024)
+    _check(load().pa_shard_prefix(ctx, _ptr(t), _ptr(out)), ctx)
+    return out
+
+
+def pa_shard_draw(ctx, all_block_max) -> int:
+    m = np.ascontiguousarray(all_block_max, dtype=np.float64)
+    n = ctypes.c_int32(0)
+    _check(load().pa_shard_draw(ctx, _ptr(m), ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def pa_shard_copies(ctx, n):
+    par = np.empty(n, np.int32)
+    fam = np.empty(n, np.int32)
+    _check(load().pa_shard_copies(ctx, _ptr(par), _ptr(fam)), ctx)
+    return par, fam
+
+
+def pa_shard_pack(ctx, replicas, dst_ptr=None) -> np.ndarray | None:
+    """Packed groups of the given increasing global replica indices: a host
+    array (uint64, ceil(n/64) x N) or, with dst_ptr, written to device memory."""
+    r = np.ascontiguousarray(replicas, dtype=np.int32)
+    if dst_ptr is not None:
+        _check(load().pa_shard_pack(ctx, _ptr(r), len(r), ctypes.c_void_p(dst_ptr), 1), ctx)
+        return None
+    N = pa_sizes(ctx)["N"]
+    out = np.empty(((len(r) + 63) // 64) * N, np.uint64)
+    _check(load().pa_shard_pack(ctx, _ptr(r), len(r), _ptr(out), 0), ctx)
+    return out
+
+
+def pa_shard_finish(ctx, groups, n_groups, parent, family, src_on_device=False):
+    par = np.ascontiguousarray(parent, dtype=np.int32)
+    fam = np.ascontiguousarray(family, dtype=np.int32)
+    g = ctypes.c_void_p(groups) if src_on_device else _ptr(np.ascontiguousarray(groups, dtype=np.uint64))
+    _check(load().pa_shard_finish(ctx, g, int(n_groups), int(bool(src_on_device)), _ptr(par), _ptr(fam)), ctx)
+
+
+def pa_shard_sums(ctx, k):
+    out = np.zeros(3, np.int64)
+    _check(load().pa_shard_sums(ctx, k, _ptr(out)), ctx)
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def pa_last_error(ctx=None) -> str:

@@ -28,6 +28,8 @@ struct pa_ctx {
     uint32_t inst, tag;
     int acc_grad;
     int sep_gather;             // the replica gather as its own launch before the sweeps
+    int shard_off, shard_total; // a shard: global replicas [shard_off, shard_off + R) of shard_total
+    int shard_copies;           // copies placed by the last pa_shard_draw
     cudaStream_t st;
     int gpb, threads, real_warps;
     int band;                   // real couplings: acceptance guard band verified on this device
@@ -62,6 +64,9 @@ struct pa_ctx {
     int32_t* counts;
     int32_t* blocksum;
     double *w, *P, *lev1, *bmax, *upper;
+    double *sh_upper, *sh_t2g, *sh_bmax;  // a shard: global prefix levels, block totals, maxima
+    int32_t *sh_pout, *sh_fout;           // a shard: parents and families of its outgoing copies
+    uint64_t* sh_stage;                   // a shard: incoming replica groups
     StepAcc* acc;
     unsigned long long *cJ, *ch;
     int8_t* tmp8;
@@ -122,11 +127,12 @@ void pa::set_global_error(const char* msg) { g_create_err = msg ? msg : ""; }
 
 // ---------------- small kernels of the orchestration ----------------
 
-__global__ void iota_kernel(int32_t* a, int32_t* b, int n)
+// a[i] = off + i (families: the global index of the initial replica), b[i] = i
+__global__ void iota_kernel(int32_t* a, int32_t* b, int n, int off)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        a[i] = i;
+        a[i] = off + i;
         if (b) b[i] = i;
     }
 }
@@ -145,7 +151,8 @@ __global__ void acc0_kernel(StepAcc* acc, double betaF0, int R, int* Rdev)
 enum {
     W_J, W_H, W_JNEG, W_JFIX, W_HFIX, W_BETAS, W_S0, W_S1, W_E32, W_E128, W_PARENT, W_FAM0, W_FAM1,
     W_COUNTS, W_BLOCKSUM, W_W, W_P, W_LEV1, W_BMAX, W_UPPER, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
-    W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_WTAB, W_SYNC, W_COUNT
+    W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_WTAB, W_SYNC,
+    W_SH_UPPER, W_SH_T2G, W_SH_BMAX, W_SH_POUT, W_SH_FOUT, W_SH_STAGE, W_COUNT
 };
 
 struct Layout {
@@ -153,7 +160,14 @@ struct Layout {
     size_t total;
 };
 
-static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps, int acc_grad)
+// incoming replica groups of a shard beyond its own groups: one partial group
+// per sending shard (at most this many shards)
+constexpr int kShardStageExtra = 64;
+
+// shard_total > 0: the context is a shard of a population of shard_total
+// replicas (global prefix levels, outgoing copies, incoming replica groups)
+static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps, int acc_grad,
+                          int shard_total = 0)
 {
     int N = (D == 3) ? L * L * L : L * L;
     int G = (R + 63) / 64;
@@ -194,6 +208,14 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
     sz[W_ICMERR] = sizeof(int);
     sz[W_SYNC] = sizeof(int) * 4;
     sz[W_WTAB] = kind == PA_PM1 ? sizeof(double) * (size_t)(D * N / 2 + 1) : 0;
+    if (shard_total > 0) {
+        sz[W_SH_UPPER] = sizeof(double) * (size_t)pa::rs_upper_size(shard_total);
+        sz[W_SH_T2G] = sizeof(double) * (size_t)pa::rs_wblocks(shard_total);
+        sz[W_SH_BMAX] = sizeof(double) * 2 * (size_t)pa::rs_wblocks(shard_total);
+        sz[W_SH_POUT] = sizeof(int32_t) * (size_t)shard_total;
+        sz[W_SH_FOUT] = sizeof(int32_t) * (size_t)shard_total;
+        sz[W_SH_STAGE] = sizeof(uint64_t) * (size_t)(G + kShardStageExtra) * N;  // incoming replica groups
+    }
     Layout lay;
     size_t off = 0;
     for (int i = 0; i < W_COUNT; ++i) {
@@ -281,6 +303,21 @@ static int validate(std::string& err, int D, int L, int kind, const float* J, co
             }
             if (N > 4096) { err = "cluster moves support N <= 4096"; return PA_EINVAL; }
         }
+        if (o->shard_total > 0) {
+            if (kind != PA_PM1 || lay != PA_LAYOUT_PACKED) { err = "shards need +-J couplings in the packed layout"; return PA_EINVAL; }
+            if (o->shard_offset < 0 || o->shard_offset % pa::kWBlock != 0 ||
+                (long long)o->shard_offset + R > o->shard_total || o->shard_total > (1 << 26)) {
+                err = "shard: offset a multiple of 1024, offset + R <= shard_total <= 2^26";
+                return PA_EINVAL;
+            }
+            if (o->populations || o->resampling || o->icm || o->accumulate_grad || o->separate_gather || o->capacity) {
+                err = "shard: fixed population, multinomial resampling, no cluster moves, gradient counts or separate gather";
+                return PA_EINVAL;
+            }
+        } else if (o->shard_total < 0 || o->shard_offset != 0) {
+            err = "shard_offset needs shard_total > 0";
+            return PA_EINVAL;
+        }
         const long long cap = capacity_of(R, n_temps, o);
         if (cap > (1 << 26)) { err = "capacity must be <= 2^26"; return PA_EINVAL; }
         if (o->resampling == PA_RESAMPLE_NEAREST && !o->populations && cap < R) {
@@ -313,7 +350,8 @@ extern "C" int pa_workspace_size(int D, int L, int kind, int R, int n_temps, con
     int lay = resolve_layout(kind, opt);
     const long long cap = capacity_of(R, n_temps, opt);
     if (cap > (1 << 26)) return PA_EINVAL;
-    Layout l = make_layout(D, L, kind, lay, (int)cap, n_temps, opt ? opt->accumulate_grad : 0);
+    Layout l = make_layout(D, L, kind, lay, (int)cap, n_temps, opt ? opt->accumulate_grad : 0,
+                           opt ? opt->shard_total : 0);
     *bytes = l.total;
     return PA_OK;
 }
@@ -348,6 +386,9 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->layout = resolve_layout(kind, &o); c->NP = (c->N + 15) / 16 * 16;
     c->seed = seed; c->inst = o.rng_instance; c->tag = o.rng_tag; c->acc_grad = o.accumulate_grad ? 1 : 0;
     c->sep_gather = o.separate_gather ? 1 : 0;
+    c->shard_off = o.shard_total > 0 ? o.shard_offset : 0;
+    c->shard_total = o.shard_total > 0 ? o.shard_total : 0;
+    c->shard_copies = 0;
     c->st = (cudaStream_t)stream;
     c->betas.assign(betas, betas + n_temps);
     c->Rk.assign(n_temps, R);
@@ -377,7 +418,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
         }
     if (nflush) c->err = "warning: " + std::to_string(nflush) + " coupling/field magnitudes below 2^-73 flushed to 0";
 
-    Layout lay = make_layout(D, L, kind, c->layout, cap, n_temps, c->acc_grad);
+    Layout lay = make_layout(D, L, kind, c->layout, cap, n_temps, c->acc_grad, c->shard_total);
     if (workspace) {
         if (ws_bytes < lay.total || ((uintptr_t)workspace & 255)) {
             g_create_err = "workspace too small or not 256-byte aligned";
@@ -427,6 +468,9 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->Rdev = (int*)at(W_RDEV);
     c->icm_err = (int*)at(W_ICMERR);
     c->sync = (int*)at(W_SYNC);
+    c->sh_upper = (double*)at(W_SH_UPPER); c->sh_t2g = (double*)at(W_SH_T2G); c->sh_bmax = (double*)at(W_SH_BMAX);
+    c->sh_pout = (int32_t*)at(W_SH_POUT); c->sh_fout = (int32_t*)at(W_SH_FOUT);
+    c->sh_stage = (uint64_t*)at(W_SH_STAGE);
     c->wtab = kind == PA_PM1 ? (double*)at(W_WTAB) : nullptr;
 
     // couplings: sign masks (+-J), fixed-point copies (real)
@@ -631,6 +675,7 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
         in.jneg = c->jneg; in.E = c->E32; in.G = G; in.R = R; in.NP = c->NP;
         if (dyn) { in.Rdev = c->Rdev + k; in.G = c->G; in.R = c->R; }
         in.c3 = pa::counter3(pa::STREAM_PLANE, c->tag, c->inst);
+        in.goff = c->shard_off / 64;  // a shard's groups carry their global index
         if (c->layout == PA_LAYOUT_PACKED) {
             // k > 0: the replica gather is fused into the sweep's tile load
             in.Sin = c->S[c->cur];
@@ -732,10 +777,10 @@ static int enqueue_init(pa_ctx* c)
     const uint32_t c3 = pa::counter3(pa::STREAM_INIT, c->tag, c->inst);
     const int R0 = c->Rk[0];
     if (c->layout == PA_LAYOUT_PACKED)
-        PA_CK(c, pa::launch_init_packed(c->S[c->cur], c->N, (R0 + 63) / 64, k0, k1, c3, c->st));
+        PA_CK(c, pa::launch_init_packed(c->S[c->cur], c->N, (R0 + 63) / 64, k0, k1, c3, c->st, c->shard_off / 64));
     else
         PA_CK(c, pa::launch_init_i8(c->S8[c->cur], c->N, c->NP, R0, k0, k1, c3, c->st));
-    iota_kernel<<<(c->R + 255) / 256, 256, 0, c->st>>>(c->fam[c->famcur], c->parent, c->R);
+    iota_kernel<<<(c->R + 255) / 256, 256, 0, c->st>>>(c->fam[c->famcur], c->parent, c->R, c->shard_off);
     acc0_kernel<<<1, 1, 0, c->st>>>(c->acc, c->betaF0, R0, c->Rdev);
     PA_CK(c, cudaGetLastError());
     c->launches += 3;
@@ -747,6 +792,10 @@ static int enqueue_step(pa_ctx* c)
 {
     const int k = c->k_next;
     if (k >= c->n_temps) { c->err = "schedule finished"; return PA_EDONE; }
+    if (c->shard_total > 0 && k > 0) {
+        c->err = "a shard resamples across shards: steps k >= 1 run with the pa_shard_* phases";
+        return PA_ESTATE;
+    }
     cudaEvent_t ev;
     if (k == 0) {
         ev = phase_begin(c, PA_PHASE_INIT);
@@ -1186,6 +1235,202 @@ extern "C" int pa_checkpoint_load(pa_ctx* c, const void* buf, size_t bytes)
         p += sct.bytes;
     }
     PA_CK(c, cudaStreamSynchronize(c->st));
+    return PA_OK;
+}
+
+// ---------------- shards of one population (Sec. V.A) ----------------
+//
+// A step k >= 1 of a shard runs in phases; between them the caller exchanges
+// small arrays among the shards (in shard order) and finally the replicas
+// each shard's new slots descend from.  Every phase synchronises the stream.
+
+static int shard_check(pa_ctx* c, int min_k)
+{
+    if (!c) return PA_EINVAL;
+    if (c->shard_total <= 0) { c->err = "not a shard"; return PA_ESTATE; }
+    if (c->k_next < min_k || c->k_next >= c->n_temps) { c->err = "no step to run"; return PA_ESTATE; }
+    return PA_OK;
+}
+
+// the resampling arguments of step k of a shard
+static void shard_args(pa_ctx* c, pa::ResampleArgs* ra)
+{
+    const int k = c->k_next;
+    std::memset(ra, 0, sizeof *ra);
+    ra->R = c->R; ra->Rn = c->shard_total; ra->kind = 0;
+    ra->gR = c->shard_total; ra->gb0 = c->shard_off / pa::kWBlock;
+    ra->E32 = c->E32;
+    ra->prev = c->acc + (k - 1); ra->cur = c->acc + k;
+    ra->w = c->w; ra->P = c->P; ra->lev1 = c->lev1; ra->t2g = c->sh_t2g;
+    ra->counts = c->counts; ra->blocksum = c->blocksum;
+    ra->parent = c->sh_pout; ra->fam_in = c->fam[c->famcur]; ra->fam_out = c->sh_fout;
+    ra->dbeta = c->betas[k] - c->betas[k - 1];
+    ra->log_R = std::log((double)c->shard_total); ra->betaF0 = c->betaF0; ra->k = k;
+    ra->wtab = c->wtab; ra->wtab_n = c->D * c->N / 2 + 1;
+    ra->key0 = (uint32_t)c->seed; ra->key1 = (uint32_t)(c->seed >> 32);
+    ra->c3 = pa::counter3(pa::STREAM_RES, c->tag, c->inst);
+}
+
+extern "C" int pa_shard_emin(pa_ctx* c, int64_t* emin)
+{
+    int rc = shard_check(c, 1);
+    if (rc) return rc;
+    if (!emin) return PA_EINVAL;
+    StepAcc a;
+    PA_CK(c, cudaMemcpyAsync(&a, c->acc + (c->k_next - 1), sizeof a, cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    *emin = a.emin_lo;
+    return PA_OK;
+}
+
+extern "C" int pa_shard_weights(pa_ctx* c, int64_t emin_global, double* host_block_totals)
+{
+    int rc = shard_check(c, 1);
+    if (rc) return rc;
+    if (!host_block_totals) return PA_EINVAL;
+    // the weights are taken relative to the lowest energy of the whole population
+    const long long em[2] = {(long long)emin_global, emin_global < 0 ? -1ll : 0ll};
+    PA_CK(c, cudaMemcpyAsync(&c->acc[c->k_next - 1].emin_lo, em, sizeof em, cudaMemcpyHostToDevice, c->st));
+    pa::ResampleArgs ra;
+    shard_args(c, &ra);
+    ra.upper = c->upper;  // the local block totals
+    PA_CK(c, pa::launch_resample_shard(ra, 0, c->st));
+    PA_CK(c, cudaMemcpyAsync(host_block_totals, c->upper, sizeof(double) * pa::rs_wblocks(c->R),
+                             cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    c->launches += 2;
+    return PA_OK;
+}
+
+extern "C" int pa_shard_prefix(pa_ctx* c, const double* host_all_totals, double* host_block_max)
+{
+    int rc = shard_check(c, 1);
+    if (rc) return rc;
+    if (!host_all_totals || !host_block_max) return PA_EINVAL;
+    const size_t nbg = (size_t)pa::rs_wblocks(c->shard_total);
+    PA_CK(c, cudaMemcpyAsync(c->sh_upper, host_all_totals, sizeof(double) * nbg, cudaMemcpyHostToDevice, c->st));
+    PA_CK(c, cudaMemcpyAsync(c->sh_t2g, host_all_totals, sizeof(double) * nbg, cudaMemcpyHostToDevice, c->st));
+    pa::ResampleArgs ra;
+    shard_args(c, &ra);
+    ra.upper = c->sh_upper;  // every shard's block totals -> the global levels >= 2
+    ra.bmax = c->bmax;       // the local block maxima
+    PA_CK(c, pa::launch_resample_shard(ra, 1, c->st));
+    PA_CK(c, cudaMemcpyAsync(host_block_max, c->bmax, sizeof(double) * pa::rs_wblocks(c->R),
+                             cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    c->launches += 2;
+    return PA_OK;
+}
+
+extern "C" int pa_shard_draw(pa_ctx* c, const double* host_all_block_max, int32_t* copies)
+{
+    int rc = shard_check(c, 1);
+    if (rc) return rc;
+    if (!host_all_block_max || !copies) return PA_EINVAL;
+    const size_t nbg = (size_t)pa::rs_wblocks(c->shard_total);
+    PA_CK(c, cudaMemcpyAsync(c->sh_bmax, host_all_block_max, sizeof(double) * nbg, cudaMemcpyHostToDevice, c->st));
+    pa::ResampleArgs ra;
+    shard_args(c, &ra);
+    ra.bmax = c->sh_bmax;
+    PA_CK(c, pa::launch_resample_shard(ra, 2, c->st));
+    const int nbs = (c->R + pa::kScanBlock - 1) / pa::kScanBlock;
+    int32_t n = 0;
+    PA_CK(c, cudaMemcpyAsync(&n, c->blocksum + nbs, sizeof n, cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    c->launches += 4;
+    c->shard_copies = n;
+    *copies = n;
+    return PA_OK;
+}
+
+extern "C" int pa_shard_copies(pa_ctx* c, int32_t* host_parent, int32_t* host_family)
+{
+    int rc = shard_check(c, 1);
+    if (rc) return rc;
+    if (!host_parent || !host_family) return PA_EINVAL;
+    pa::ResampleArgs ra;
+    shard_args(c, &ra);
+    PA_CK(c, pa::launch_resample_shard(ra, 3, c->st));
+    const size_t n = (size_t)c->shard_copies;
+    PA_CK(c, cudaMemcpyAsync(host_parent, c->sh_pout, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaMemcpyAsync(host_family, c->sh_fout, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    c->launches += 1;
+    return PA_OK;
+}
+
+extern "C" int pa_shard_pack(pa_ctx* c, const int32_t* host_replicas, int n, void* dst, int dst_on_device)
+{
+    int rc = shard_check(c, 1);
+    if (rc) return rc;
+    if (n < 0 || n > c->R || (n > 0 && (!host_replicas || !dst))) return PA_EINVAL;
+    if (n == 0) return PA_OK;
+    for (int i = 0; i < n; ++i)
+        if (host_replicas[i] < c->shard_off || host_replicas[i] >= c->shard_off + c->R ||
+            (i > 0 && host_replicas[i] <= host_replicas[i - 1])) {
+            c->err = "pa_shard_pack: replicas must be increasing global indices of this shard";
+            return PA_EINVAL;
+        }
+    // the local indices of the replicas, then the packed gather of those replicas
+    std::vector<int32_t> loc(n);
+    for (int i = 0; i < n; ++i) loc[i] = host_replicas[i] - c->shard_off;
+    PA_CK(c, cudaMemcpyAsync(c->sh_pout, loc.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->st));
+    const int ng = (n + 63) / 64;
+    uint64_t* out = c->sh_stage;  // scratch until pa_shard_finish receives
+    PA_CK(c, pa::launch_gather(c->S[c->cur], out, nullptr, nullptr, c->sh_pout, c->N, c->NP, n, nullptr, c->st));
+    PA_CK(c, cudaMemcpyAsync(dst, out, sizeof(uint64_t) * (size_t)ng * c->N,
+                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    c->launches += 1;
+    return PA_OK;
+}
+
+extern "C" int pa_shard_finish(pa_ctx* c, const void* groups, int n_groups, int src_on_device,
+                               const int32_t* host_parent, const int32_t* host_family)
+{
+    int rc = shard_check(c, 1);
+    if (rc) return rc;
+    const int G = (c->R + 63) / 64;
+    if (!groups || !host_parent || !host_family || n_groups < 1 || n_groups > G + kShardStageExtra) {
+        c->err = "pa_shard_finish: need 1..(own groups + 64) incoming groups, parents and families";
+        return PA_EINVAL;
+    }
+    for (int j = 0; j < c->R; ++j)
+        if (host_parent[j] < 0 || host_parent[j] >= 64 * n_groups) {
+            c->err = "pa_shard_finish: a parent index is outside the incoming groups";
+            return PA_EINVAL;
+        }
+    PA_CK(c, cudaMemcpyAsync(c->sh_stage, groups, sizeof(uint64_t) * (size_t)n_groups * c->N,
+                             src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+    StepPlan pl;
+    plan_step(c, &pl);  // advances k, the ping-pong buffers and the family buffer
+    PA_CK(c, cudaMemcpyAsync(c->parent, host_parent, sizeof(int32_t) * c->R, cudaMemcpyHostToDevice, c->st));
+    PA_CK(c, cudaMemcpyAsync(c->fam[c->famcur], host_family, sizeof(int32_t) * c->R, cudaMemcpyHostToDevice,
+                             c->st));
+    pl.pk.i.Sin = c->sh_stage;  // the gather reads the incoming replicas
+    pl.pk.i.parent = c->parent;
+    cudaEvent_t ev = phase_begin(c, PA_PHASE_SWEEP);
+    PA_CK(c, pa::launch_sweep_packed(c->D, c->L, pl.pk, c->gpb, c->threads, c->st));
+    phase_end(c, PA_PHASE_SWEEP, ev);
+    ev = phase_begin(c, PA_PHASE_OBSERVE);
+    PA_CK(c, pa::launch_observe(pl.ob, c->st));
+    phase_end(c, PA_PHASE_OBSERVE, ev);
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    c->launches += 2;
+    return PA_OK;
+}
+
+extern "C" int pa_shard_sums(pa_ctx* c, int k, int64_t* sums)
+{
+    if (!c || !sums) return PA_EINVAL;
+    if (c->shard_total <= 0) { c->err = "not a shard"; return PA_ESTATE; }
+    if (k < 0 || k >= c->k_next) { c->err = "step not run yet"; return PA_ESTATE; }
+    StepAcc a;
+    PA_CK(c, cudaMemcpyAsync(&a, c->acc + k, sizeof a, cudaMemcpyDeviceToHost, c->st));
+    PA_CK(c, cudaStreamSynchronize(c->st));
+    sums[0] = a.sumE;
+    sums[1] = a.sumE2;
+    sums[2] = a.emin_lo;
     return PA_OK;
 }
 

@@ -48,6 +48,7 @@ struct PackedInst {
     const int* Rdev;         // population in device memory (or null: R); G, R then size the grid
     int G, R, NP;
     uint32_t c3;             // Philox counter word 3 of the PLANE stream
+    int goff;                // global index of group 0 (a shard of a larger population; else 0)
 };
 struct PackedSweepArgs {
     PackedStep s;
@@ -58,7 +59,7 @@ cudaError_t launch_sweep_packed(int D, int L, const PackedSweepArgs& a, int gpb,
 bool packed_supported(int D, int L);
 void packed_default_shape(int D, int L, int* gpb, int* threads);
 cudaError_t launch_init_packed(uint64_t* S, int N, int G, uint32_t k0, uint32_t k1, uint32_t c3,
-                               cudaStream_t st);
+                               cudaStream_t st, int goff = 0);
 cudaError_t launch_unpack_packed(const uint64_t* S, int8_t* out, int N, int r0, int n, cudaStream_t st);
 cudaError_t launch_overlap_packed(const uint64_t* A, const uint64_t* B, int N, int R,
                                   unsigned long long* hist, cudaStream_t st);
@@ -96,6 +97,7 @@ struct RealInst {
     const int* Rdev;         // population in device memory (or null: R); R then sizes the grid
     int R, NP;
     uint32_t c3;             // Philox counter word 3 of the WORD stream
+    int roff;                // global index of replica 0 (a shard of a larger population; else 0)
 };
 struct RealSweepArgs {
     RealStep s;
@@ -111,7 +113,7 @@ cudaError_t accept_band_check(cudaStream_t st, unsigned long long* violations, d
 // the verdict for the current device, checked once per process
 int accept_band_ok(cudaStream_t st);
 cudaError_t launch_init_i8(int8_t* S, int N, int NP, int R, uint32_t k0, uint32_t k1, uint32_t c3,
-                           cudaStream_t st);
+                           cudaStream_t st, int goff = 0);
 cudaError_t launch_overlap_i8(const int8_t* A, const int8_t* B, int N, int NP, int R,
                               unsigned long long* hist, cudaStream_t st);
 
@@ -172,6 +174,14 @@ struct ResampleArgs {
     double* bmax;                // [2 rs_wblocks(R)] largest prefix sum of each weights block,
                                  // then the largest before each block (running maximum)
     double* upper;               // [rs_upper_size(R)] levels 2, 3, ... of the prefix
+    // a shard of a population of gR replicas spread over several contexts
+    // (gR = 0: not sharded): the local replicas are the global replicas
+    // [kWBlock gb0, kWBlock gb0 + R); upper and bmax then hold the global
+    // levels (rs_upper_size(gR), 2 rs_wblocks(gR)), t2g the global block
+    // totals, the draws are the gR global ones (only those landing on local
+    // replicas are counted), and parents are written as global indices
+    int gR, gb0;
+    const double* t2g;
     int32_t* counts;             // [R] copy numbers (zero on entry, zeroed again on exit)
     int32_t* blocksum;           // [nblocks] scratch for the count scan
     int32_t* parent;             // [R] out
@@ -200,6 +210,8 @@ __host__ __device__ constexpr inline int rs_upper_size(int R)
 }
 constexpr int kScanBlock = 4096; // elements per block of the copy-number scan
 cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st);
+// one phase (0..3) of a shard's resampling (a.gR > 0, a.sync null)
+cudaError_t launch_resample_shard(const ResampleArgs& a, int phase, cudaStream_t st);
 // all instances of a batch at once: tab[i] describes instance i (device memory)
 cudaError_t launch_resample_batched(const ResampleArgs* tab, int n_inst, int maxR, cudaStream_t st);
 

@@ -61,20 +61,20 @@ cudaError_t launch_sweep_packed(int D, int L, const PackedSweepArgs& a, int gpb,
 // ---------------- init, gather, unpack, overlap ----------------
 
 // Sec. II.B: replicas start at random (beta = 0).  INIT stream word per (group, site).
-__global__ void init_packed_kernel(uint64_t* S, int N, int G, uint32_t k0, uint32_t k1, uint32_t c3)
+__global__ void init_packed_kernel(uint64_t* S, int N, int G, uint32_t k0, uint32_t k1, uint32_t c3, int goff)
 {
     size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)N * G) return;
     int g = (int)(t / N), i = (int)(t - (size_t)g * N);
-    u32x4 o = philox((uint32_t)i, (uint32_t)g, 0u, c3, k0, k1);
+    u32x4 o = philox((uint32_t)i, (uint32_t)(g + goff), 0u, c3, k0, k1);
     S[t] = (uint64_t)o.x | ((uint64_t)o.y << 32);
 }
 
 cudaError_t launch_init_packed(uint64_t* S, int N, int G, uint32_t k0, uint32_t k1, uint32_t c3,
-                               cudaStream_t st)
+                               cudaStream_t st, int goff)
 {
     size_t n = (size_t)N * G;
-    init_packed_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, N, G, k0, k1, c3);
+    init_packed_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, N, G, k0, k1, c3, goff);
     return cudaGetLastError();
 }
 

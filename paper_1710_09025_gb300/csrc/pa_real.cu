@@ -159,13 +159,13 @@ cudaError_t launch_sweep_real(int D, int L, const RealSweepArgs& a, int warps, i
 }
 
 // Sec. II.B: random initial replicas; same INIT stream as the packed layout.
-__global__ void init_i8_kernel(int8_t* S, int N, int NP, int R, uint32_t k0, uint32_t k1, uint32_t c3)
+__global__ void init_i8_kernel(int8_t* S, int N, int NP, int R, uint32_t k0, uint32_t k1, uint32_t c3, int goff)
 {
     const int G = (R + 63) / 64;
     size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)N * G) return;
     int g = (int)(t / N), i = (int)(t - (size_t)g * N);
-    u32x4 o = philox((uint32_t)i, (uint32_t)g, 0u, c3, k0, k1);
+    u32x4 o = philox((uint32_t)i, (uint32_t)(g + goff), 0u, c3, k0, k1);
     uint64_t w = (uint64_t)o.x | ((uint64_t)o.y << 32);
     for (int j = 0; j < 64; ++j) {
         int r = 64 * g + j;
@@ -175,12 +175,12 @@ __global__ void init_i8_kernel(int8_t* S, int N, int NP, int R, uint32_t k0, uin
 }
 
 cudaError_t launch_init_i8(int8_t* S, int N, int NP, int R, uint32_t k0, uint32_t k1, uint32_t c3,
-                           cudaStream_t st)
+                           cudaStream_t st, int goff)
 {
     cudaError_t e = cudaMemsetAsync(S, 0x01, (size_t)R * NP, st);
     if (e != cudaSuccess) return e;
     size_t n = (size_t)N * ((R + 63) / 64);
-    init_i8_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, N, NP, R, k0, k1, c3);
+    init_i8_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, N, NP, R, k0, k1, c3, goff);
     return cudaGetLastError();
 }
 

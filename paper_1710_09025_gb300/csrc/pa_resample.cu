@@ -143,7 +143,7 @@ __device__ __forceinline__ void rs_top_body(const ResampleArgs& a)
 {
     constexpr int kMaxLev = 8;  // kFan^(kMaxLev+1) > 2^31 weights
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int R = rs_src(a);
+    const int R = a.gR ? a.gR : rs_src(a);  // a shard sums the global block totals
     int base[kMaxLev], len[kMaxLev], nl = 0;
     int n = rs_wblocks(R), off = 0;
     for (;;) {
@@ -205,12 +205,15 @@ __device__ __forceinline__ void rs_finalize_body(const ResampleArgs& a, int b)
     const int i0 = b * kWBlock;
     if (i0 >= R) return;  // block-uniform
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cg0 = a.gb0 * kFan;  // global index of local run 0 (0 unless a shard)
     if (tid < kFan) {  // Q1 of the run before run c = b kFan + tid (one addition per run)
         const int c = b * kFan + tid;
         double q = 0.0;
-        if (c > 0 && c * kFan < R) {
-            const int cb = (c - 1) / kFan;
-            const double l1 = a.lev1[c - 1];
+        if (cg0 + c > 0 && c * kFan < R) {
+            const int cb = (cg0 + c - 1) / kFan;  // global block of run c - 1
+            // l1 of run c - 1; before a shard's first run it is the last run of
+            // the previous (remote) block, whose l1 is that block's total
+            const double l1 = c > 0 ? a.lev1[c - 1] : a.t2g[cb];
             q = cb == 0 ? l1 : __dadd_rn(a.upper[cb - 1], l1);
         }
         s_q[tid] = q;
@@ -224,7 +227,7 @@ __device__ __forceinline__ void rs_finalize_body(const ResampleArgs& a, int b)
         long long x = 0;
         if (i < R) {
             const double l = a.P[i];
-            x = dbits(i < kFan ? l : __dadd_rn(s_q[(tid * PER + j) / kFan], l));
+            x = dbits(cg0 == 0 && i < kFan ? l : __dadd_rn(s_q[(tid * PER + j) / kFan], l));
         }
         m = max(m, x);
         v[j] = m;  // inclusive maximum within this thread's weights
@@ -260,7 +263,7 @@ __device__ __forceinline__ void rs_blockmax_body(const ResampleArgs& a)
     __shared__ long long s_w[32];
     __shared__ long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int R = rs_src(a);
+    const int R = a.gR ? a.gR : rs_src(a);  // a shard: the global block maxima
     const int nb = rs_wblocks(R);
     if (tid == 0) s_carry = 0;
     __syncthreads();
@@ -375,6 +378,49 @@ __device__ __forceinline__ void rs_draws_body(const ResampleArgs& a, int q)
     }
     atomicAdd(&a.counts[lo], 1);
 }
+// A shard's draws: all gR global draws are evaluated, a draw's weights block
+// is found from the global block ends, and only draws that land on a local
+// block are resolved (bisection in the local P) and counted.
+__device__ __forceinline__ void rs_draws_shard_body(const ResampleArgs& a, int q)
+{
+    __shared__ long long s_end[kMaxSeg];
+    const int nb = rs_wblocks(a.gR), nloc = rs_wblocks(a.R);
+    const int sb = rs_seg_blocks(nb), nseg = (nb + sb - 1) / sb;
+    const double S = a.cur->S;
+    // largest P up to the end of block b: the largest before block b + 1, or S
+    auto block_end = [&](int b) { return b + 1 < nb ? dbits(a.bmax[nb + b + 1]) : dbits(S); };
+    for (int k = threadIdx.x; k < nseg; k += blockDim.x) s_end[k] = block_end(min(nb - 1, k * sb + sb - 1));
+    __syncthreads();
+    if (q >= a.Rn) return;
+    const u32x4 o = philox((uint32_t)q, (uint32_t)a.k, 0u, a.c3, a.key0, a.key1);
+    const long long x = dbits(__dmul_rn(uniform53(o.x, o.y), S));  // x >= 0
+    int lo = 0, hi = nseg;
+    while (lo < hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (x < s_end[mid]) hi = mid; else lo = mid + 1;
+    }
+    const bool strict = lo < nseg;  // some P exceeds x; else x == S: the first P >= x
+    int b0 = strict ? lo * sb : 0, b1 = strict ? min(nb - 1, lo * sb + sb - 1) : nb - 1;
+    while (b0 < b1) {  // the first block whose end exceeds x (or reaches x)
+        const int mid = b0 + ((b1 - b0) >> 1);
+        const long long e = block_end(mid);
+        if (strict ? x < e : e >= x) b1 = mid; else b0 = mid + 1;
+    }
+    const int bl = b0 - a.gb0;
+    if (bl < 0 || bl >= nloc) return;  // another shard's draw
+    const long long before = dbits(a.bmax[nb + b0]);
+    int i = bl * kWBlock, j = min(a.R, i + kWBlock) - 1;
+    while (i < j) {
+        const int mid = i + ((j - i) >> 1);
+        const long long p = max(before, dbits(a.P[mid]));
+        if (strict ? x < p : p >= x) j = mid; else i = mid + 1;
+    }
+    atomicAdd(&a.counts[i], 1);
+}
+__global__ void __launch_bounds__(kDrawThreads) rs_draws_shard_kernel(ResampleArgs a)
+{
+    rs_draws_shard_body(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
 __global__ void __launch_bounds__(kDrawThreads) rs_draws_kernel(ResampleArgs a)
 {
     rs_draws_body(a, blockIdx.x * blockDim.x + threadIdx.x);
@@ -445,7 +491,9 @@ __device__ __forceinline__ int rs_scan_blocks_body(int32_t* blocksum, int nb)
 __device__ __forceinline__ void rs_scan_finish(const ResampleArgs& a)
 {
     const int R = rs_src(a);
-    const int total = rs_scan_blocks_body(a.blocksum, (R + kScanBlock - 1) / kScanBlock);
+    const int nbs = (R + kScanBlock - 1) / kScanBlock;
+    const int total = rs_scan_blocks_body(a.blocksum, nbs);
+    a.blocksum[nbs] = total;  // the copies placed (a shard reads it)
     if (a.Rdst) {  // the drawn population, copies beyond the capacity dropped
         const int Rn = min(total, a.cap);
         *a.Rdst = Rn;
@@ -498,6 +546,7 @@ __device__ __forceinline__ void rs_fill_body(const ResampleArgs& a, int b)
     }
     __syncthreads();
     int off = a.blocksum[b] + ws[warp] + (incl - s);
+    const int pbase = a.gb0 * kWBlock;  // a shard writes global replica indices
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
         const int i = i0 + t;
@@ -505,7 +554,7 @@ __device__ __forceinline__ void rs_fill_body(const ResampleArgs& a, int b)
             const int f = a.fam_in[i];
             const int n = min(c[t], max(cap - off, 0));  // slots past the capacity are dropped
             for (int u = 0; u < n; ++u) {
-                a.parent[off + u] = i;
+                a.parent[off + u] = pbase + i;
                 a.fam_out[off + u] = f;
             }
             off += c[t];
@@ -526,7 +575,8 @@ __global__ void __launch_bounds__(1024) rs_fill_batched(const ResampleArgs* tab)
 cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
 {
     const int nb = (a.R + kScanBlock - 1) / kScanBlock;
-    if (a.wtab) rs_table_kernel<<<(a.wtab_n + 255) / 256, 256, 0, st>>>(a);
+    // one level per thread, small blocks spread over the SMs (FP64-bound)
+    if (a.wtab) rs_table_kernel<<<(a.wtab_n + 31) / 32, 32, 0, st>>>(a);
     rs_weights_kernel<<<rs_wblocks(a.R), kWThreads, 0, st>>>(a);
     if (!a.sync) rs_top_kernel<<<1, kWBlock, 0, st>>>(a);
     rs_finalize_kernel<<<rs_wblocks(a.R), kWThreads, 0, st>>>(a);
@@ -538,6 +588,33 @@ cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t st)
     rs_blocksum_kernel<<<nb, 1024, 0, st>>>(a);
     if (!a.sync) rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a);
     rs_fill_kernel<<<nb, 1024, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// the phases of a shard's resampling (the host exchanges the block totals,
+// the block maxima and the copy totals between them)
+cudaError_t launch_resample_shard(const ResampleArgs& a, int phase, cudaStream_t st)
+{
+    const int nb = (a.R + kScanBlock - 1) / kScanBlock;
+    switch (phase) {
+    case 0:  // weights, levels 0 and 1 of the local blocks -> local block totals in upper
+        if (a.wtab) rs_table_kernel<<<(a.wtab_n + 31) / 32, 32, 0, st>>>(a);
+        rs_weights_kernel<<<rs_wblocks(a.R), kWThreads, 0, st>>>(a);
+        break;
+    case 1:  // global levels >= 2 (upper holds every shard's block totals), local P, block maxima
+        rs_top_kernel<<<1, kWBlock, 0, st>>>(a);
+        rs_finalize_kernel<<<rs_wblocks(a.R), kWThreads, 0, st>>>(a);
+        break;
+    case 2:  // running maximum over every shard's blocks, S, ln Q; draws; copy totals
+        rs_blockmax_kernel<<<1, kWBlock, 0, st>>>(a);
+        rs_draws_shard_kernel<<<(a.Rn + kDrawThreads - 1) / kDrawThreads, kDrawThreads, 0, st>>>(a);
+        rs_blocksum_kernel<<<nb, 1024, 0, st>>>(a);
+        rs_scan_blocks_kernel<<<1, 32, 0, st>>>(a);
+        break;
+    default:  // placement: global parent indices and families of the local copies
+        rs_fill_kernel<<<nb, 1024, 0, st>>>(a);
+        break;
+    }
     return cudaGetLastError();
 }
 
@@ -602,8 +679,11 @@ __device__ __forceinline__ void observe_partial_body(const ObsArgs& a)
                 }
                 e = lo;
             }
-            const double c = (double)(e - j);
-            clnc = __fma_rn(c, log(c), clnc);
+            // c ln c of the run; a run of one adds exactly 0 (GB300's FP64 log is costly)
+            if (e - j > 1) {
+                const double c = (double)(e - j);
+                clnc = __fma_rn(c, log(c), clnc);
+            }
         }
     }
     // fixed shuffle trees; the FP64 ones only where they can add something

@@ -410,7 +410,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     for (int e = atomicAdd(cnt_r + 1, 1); e < n; e = atomicAdd(cnt_r + 1, 1)) {
                         const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
                         uint64_t acc2 = 0;
-                        compare_mode1((uint32_t)q2, (uint32_t)(g0 + gl2), hs, QU[e], acc2);
+                        compare_mode1((uint32_t)q2, (uint32_t)(g0 + in.goff + gl2), hs, QU[e], acc2);
                         sm[(gl2 * 2 + p) * NH + q2] ^= acc2;
                     }
                     __syncthreads();
@@ -422,7 +422,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     uint64_t sw0, b0, b1, b2, down, acc, U;
                     classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
                     start(b0, b1, b2, down, acc, U);
-                    compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
+                    compare_mode02((uint32_t)q, (uint32_t)(g0 + in.goff + t / NH), hs, U, b0, b1, acc,
                                    std::integral_constant<int, 0>{}, std::integral_constant<int, 16>{});
                     cur[q] = sw0 ^ acc;
                 }
@@ -451,7 +451,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                             uint64_t sw0, b2, down, acc;
                             classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
                             start(b0, b1, b2, down, acc, U);
-                            compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
+                            compare_mode02((uint32_t)q, (uint32_t)(g0 + in.goff + t / NH), hs, U, b0, b1, acc,
                                            std::integral_constant<int, 0>{}, std::integral_constant<int, KLATE>{});
                             cur[q] = sw0 ^ acc;
                         }
@@ -473,7 +473,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                         const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
                         const uint64_t A = QU[e], Bm = QB[e];
                         uint64_t U2 = A | Bm, acc2 = 0;
-                        compare_mode02((uint32_t)q2, (uint32_t)(g0 + gl2), hs, U2, A & Bm, Bm & ~A, acc2,
+                        compare_mode02((uint32_t)q2, (uint32_t)(g0 + in.goff + gl2), hs, U2, A & Bm, Bm & ~A, acc2,
                                        std::integral_constant<int, KLATE>{}, std::integral_constant<int, 16>{});
                         sm[(gl2 * 2 + p) * NH + q2] ^= acc2;  // lanes accepted in the queue
                     }
@@ -735,7 +735,7 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
             const int8_t* oth = T + (p ^ 1) * NH * 32;
             int8_t* cur = T + p * NH * 32;
             for (int blk = warp; blk < NB; blk += WARPS) {
-                const u32x4 o = philox_rk((uint32_t)blk, hsw, (uint32_t)r, c3, s.rk);
+                const u32x4 o = philox_rk((uint32_t)blk, hsw, (uint32_t)(r + in.roff), c3, s.rk);
                 const uint32_t rs[4] = {o.x, o.y, o.z, o.w};
                 // the four sites of one random-number block are independent (same
                 // parity): fields and energy changes first, then decisions, then stores
