@@ -310,8 +310,10 @@ static int validate(std::string& err, int D, int L, int kind, const float* J, co
                 err = "shard: offset a multiple of 1024, offset + R <= shard_total <= 2^26";
                 return PA_EINVAL;
             }
-            if (o->populations || o->resampling || o->icm || o->accumulate_grad || o->separate_gather || o->capacity) {
-                err = "shard: fixed population, multinomial resampling, no cluster moves, gradient counts or separate gather";
+            if (o->populations || o->resampling || o->icm || o->accumulate_grad || o->separate_gather || o->capacity ||
+                o->threads || o->groups_per_block) {
+                err = "shard: fixed population, multinomial resampling, default tile; no cluster moves, gradient "
+                      "counts or separate gather";
                 return PA_EINVAL;
             }
         } else if (o->shard_total < 0 || o->shard_offset != 0) {

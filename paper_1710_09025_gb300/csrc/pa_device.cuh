@@ -87,6 +87,40 @@ __device__ __forceinline__ u32x4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2
     return {c0, c1, c2, c3};
 }
 
+// The same with counter word 2 taken as c2 + d, given add2 = d * 0xCD9E8D57
+// as a 64-bit product: word 2 enters Philox only through its first-round
+// product, and (c2 + d) M = c2 M + d M exactly while c2 + d < 2^32, so the
+// offset rides in the multiply's addend (identical output to
+// philox_rk(c0, c1, c2 + d, c3, rk)).
+__device__ __forceinline__ u32x4 philox_rk_add2(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                const uint32_t (&rk)[20], uint64_t add2)
+{
+    {
+        const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u, p2 = (uint64_t)c2 * 0xCD9E8D57u + add2;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo2 = (uint32_t)p2, hi2 = (uint32_t)(p2 >> 32);
+        const uint32_t n0 = hi2 ^ c1 ^ rk[0];
+        const uint32_t n2 = hi0 ^ c3 ^ rk[1];
+        c0 = n0;
+        c1 = lo2;
+        c2 = n2;
+        c3 = lo0;
+    }
+#pragma unroll
+    for (int rnd = 1; rnd < 10; ++rnd) {
+        const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u, p2 = (uint64_t)c2 * 0xCD9E8D57u;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo2 = (uint32_t)p2, hi2 = (uint32_t)(p2 >> 32);
+        const uint32_t n0 = hi2 ^ c1 ^ rk[2 * rnd];
+        const uint32_t n2 = hi0 ^ c3 ^ rk[2 * rnd + 1];
+        c0 = n0;
+        c1 = lo2;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return {c0, c1, c2, c3};
+}
+
 // 53-bit uniform in [0, 1) from two 32-bit words
 PA_HD double uniform53(uint32_t a, uint32_t b)
 {

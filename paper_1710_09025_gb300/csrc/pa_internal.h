@@ -97,7 +97,6 @@ struct RealInst {
     const int* Rdev;         // population in device memory (or null: R); R then sizes the grid
     int R, NP;
     uint32_t c3;             // Philox counter word 3 of the WORD stream
-    int roff;                // global index of replica 0 (a shard of a larger population; else 0)
 };
 struct RealSweepArgs {
     RealStep s;

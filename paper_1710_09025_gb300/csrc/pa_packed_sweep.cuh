@@ -7,20 +7,20 @@
 
 namespace pa {
 
-template <int D, int L, int GPB, int THREADS, bool I8>
+template <int D, int L, int GPB, int THREADS, bool I8, bool SHARD = false>
 __global__ void __launch_bounds__(THREADS, 4) sweep_packed_kernel(PackedSweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_packed[];
-    sweep_packed_tile<D, L, GPB, THREADS, I8>(a.s, a.i, blockIdx.x * GPB, smem_packed);
+    sweep_packed_tile<D, L, GPB, THREADS, I8, true, SHARD>(a.s, a.i, blockIdx.x * GPB, smem_packed);
 }
 
 // ---------------- shapes and dispatch ----------------
 
-template <int D, int L, int GPB, int THREADS, bool I8>
+template <int D, int L, int GPB, int THREADS, bool I8, bool SHARD = false>
 static cudaError_t launch_one(const PackedSweepArgs& a, cudaStream_t st)
 {
     const size_t smem = PackedShape<D, L, GPB, THREADS>::SMEM;
-    auto kern = sweep_packed_kernel<D, L, GPB, THREADS, I8>;
+    auto kern = sweep_packed_kernel<D, L, GPB, THREADS, I8, SHARD>;
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -37,6 +37,10 @@ static cudaError_t launch_dl(const PackedSweepArgs& a, int gpb, int threads, cud
 {
     constexpr Shape s = default_shape<D, L>();
     const bool i8 = a.i.S8_out != nullptr;
+    if (a.i.goff != 0) {  // a shard (packed words, default shape)
+        if (i8 || gpb != s.gpb || threads != s.threads) return cudaErrorInvalidConfiguration;
+        return launch_one<D, L, s.gpb, s.threads, false, true>(a, st);
+    }
     // the one tuned alternative: twice the groups per block, same thread count
     if (gpb == 2 * s.gpb && threads == s.threads)
         return i8 ? launch_one<D, L, 2 * s.gpb, s.threads, true>(a, st)

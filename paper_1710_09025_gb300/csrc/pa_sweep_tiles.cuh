@@ -130,7 +130,10 @@ template <int D, int L> __host__ __device__ constexpr Shape default_shape()
 // groups [g0, g0 + GPB) of one instance; smem holds PackedShape::SMEM bytes
 // LATE: allow the late compaction of modes 0 and 2 (the single-instance
 // kernels; the disorder batch measured slower with it)
-template <int D, int L, int GPB, int THREADS, bool I8, bool LATE = true>
+// SHARD: the instance is a shard of a larger population; its PLANE counters
+// carry the global group index g0 + in.goff (a separate instantiation, so
+// that the counters of every other launch cost nothing extra)
+template <int D, int L, int GPB, int THREADS, bool I8, bool LATE = true, bool SHARD = false>
 __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const PackedInst& in, int g0,
                                                   unsigned char* smem)
 {
@@ -147,6 +150,13 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     const int G = in.Rdev ? (R + 63) >> 6 : in.G;
     if (g0 >= G) return;  // block-uniform: past the population held in device memory
     const uint32_t c3 = in.c3;
+    // a shard's groups carry their global index in the PLANE counters:
+    // 16 goff added to counter word 2 through its first-round product
+    const uint64_t gadd = SHARD ? (uint64_t)(16u * (uint32_t)in.goff) * 0xCD9E8D57ull : 0ull;
+    auto plane_call = [&](uint32_t q, uint32_t hs, uint32_t c2) {
+        if constexpr (SHARD) return philox_rk_add2(q, hs, c2, c3, s.rk, gadd);
+        else return philox_rk(q, hs, c2, c3, s.rk);
+    };
     const int32_t* __restrict__ parent = in.parent;
     const int ng = min(GPB, G - g0);
     const int tid = threadIdx.x;
@@ -273,7 +283,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             if (!U) break;
-            const u32x4 o = philox_rk(q, hs, 16u * g + (uint32_t)m, c3, s.rk);
+            const u32x4 o = plane_call(q, hs, 16u * g + (uint32_t)m);
             // the dE = 4 class has n = 2 unsatisfied bonds in 3D (v10), n = 1 in 2D (v01)
             plane_step_uniform((uint64_t)o.x | ((uint64_t)o.y << 32),
                                (D == 3) ? s.v10[2 * m] : s.v01[2 * m], U, acc);
@@ -292,7 +302,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
 #pragma unroll
             for (int m = m0; m < m1; ++m) {
                 if (!U) break;
-                const u32x4 o = philox_rk(q, hs, 16u * g + (uint32_t)m, c3, s.rk);
+                const u32x4 o = plane_call(q, hs, 16u * g + (uint32_t)m);
                 const uint64_t p0 = (uint64_t)o.x | ((uint64_t)o.y << 32);
                 const uint64_t p1 = (uint64_t)o.z | ((uint64_t)o.w << 32);
                 if ((zp >> (2 * m)) & 1u) U &= ~p0;
@@ -307,7 +317,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
 #pragma unroll
             for (int m = m0; m < m1; ++m) {
                 if (!U) break;
-                const u32x4 o = philox_rk(q, hs, 16u * g + (uint32_t)m, c3, s.rk);
+                const u32x4 o = plane_call(q, hs, 16u * g + (uint32_t)m);
                 const uint64_t p0 = (uint64_t)o.x | ((uint64_t)o.y << 32);
                 const uint64_t p1 = (uint64_t)o.z | ((uint64_t)o.w << 32);
                 if ((zp >> (2 * m)) & 1u) U &= ~p0;
@@ -320,7 +330,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
 #pragma unroll
             for (int m = m0; m < m1; ++m) {
                 if (!U) break;
-                const u32x4 o = philox_rk(q, hs, 16u * g + (uint32_t)m, c3, s.rk);
+                const u32x4 o = plane_call(q, hs, 16u * g + (uint32_t)m);
                 plane_step((uint64_t)o.x | ((uint64_t)o.y << 32), s.v00[2 * m], s.v01[2 * m],
                            s.v10[2 * m], b0, b1, U, acc);
                 plane_step((uint64_t)o.z | ((uint64_t)o.w << 32), s.v00[2 * m + 1], s.v01[2 * m + 1],
@@ -410,7 +420,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     for (int e = atomicAdd(cnt_r + 1, 1); e < n; e = atomicAdd(cnt_r + 1, 1)) {
                         const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
                         uint64_t acc2 = 0;
-                        compare_mode1((uint32_t)q2, (uint32_t)(g0 + in.goff + gl2), hs, QU[e], acc2);
+                        compare_mode1((uint32_t)q2, (uint32_t)(g0 + gl2), hs, QU[e], acc2);
                         sm[(gl2 * 2 + p) * NH + q2] ^= acc2;
                     }
                     __syncthreads();
@@ -422,7 +432,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     uint64_t sw0, b0, b1, b2, down, acc, U;
                     classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
                     start(b0, b1, b2, down, acc, U);
-                    compare_mode02((uint32_t)q, (uint32_t)(g0 + in.goff + t / NH), hs, U, b0, b1, acc,
+                    compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
                                    std::integral_constant<int, 0>{}, std::integral_constant<int, 16>{});
                     cur[q] = sw0 ^ acc;
                 }
@@ -451,7 +461,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                             uint64_t sw0, b2, down, acc;
                             classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
                             start(b0, b1, b2, down, acc, U);
-                            compare_mode02((uint32_t)q, (uint32_t)(g0 + in.goff + t / NH), hs, U, b0, b1, acc,
+                            compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
                                            std::integral_constant<int, 0>{}, std::integral_constant<int, KLATE>{});
                             cur[q] = sw0 ^ acc;
                         }
@@ -473,7 +483,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                         const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
                         const uint64_t A = QU[e], Bm = QB[e];
                         uint64_t U2 = A | Bm, acc2 = 0;
-                        compare_mode02((uint32_t)q2, (uint32_t)(g0 + in.goff + gl2), hs, U2, A & Bm, Bm & ~A, acc2,
+                        compare_mode02((uint32_t)q2, (uint32_t)(g0 + gl2), hs, U2, A & Bm, Bm & ~A, acc2,
                                        std::integral_constant<int, KLATE>{}, std::integral_constant<int, 16>{});
                         sm[(gl2 * 2 + p) * NH + q2] ^= acc2;  // lanes accepted in the queue
                     }
@@ -735,7 +745,7 @@ __device__ __forceinline__ void sweep_real_tile(const RealStep& s, const RealIns
             const int8_t* oth = T + (p ^ 1) * NH * 32;
             int8_t* cur = T + p * NH * 32;
             for (int blk = warp; blk < NB; blk += WARPS) {
-                const u32x4 o = philox_rk((uint32_t)blk, hsw, (uint32_t)(r + in.roff), c3, s.rk);
+                const u32x4 o = philox_rk((uint32_t)blk, hsw, (uint32_t)r, c3, s.rk);
                 const uint32_t rs[4] = {o.x, o.y, o.z, o.w};
                 // the four sites of one random-number block are independent (same
                 // parity): fields and energy changes first, then decisions, then stores

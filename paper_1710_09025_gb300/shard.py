@@ -74,13 +74,13 @@ def assemble(incoming: dict, offset: int, R: int):
 class Shard:
     """One shard: a library context holding its range of the population."""
 
-    def __init__(self, P, D, L, J, R_total, betas, n_sweeps, seed, rank, world, rng_instance=0):
+    def __init__(self, P, D, L, J, R_total, betas, n_sweeps, seed, rank, world, rng_instance=0, rng_tag=0):
         self.P = P
         self.rank, self.world = rank, world
         self.ranges = shard_ranges(R_total, world)
         self.offset, self.R = self.ranges[rank]
         opts = P.pa_options_default(layout=P.PA_LAYOUT_PACKED, shard_offset=self.offset,
-                                    shard_total=R_total, rng_instance=rng_instance)
+                                    shard_total=R_total, rng_instance=rng_instance, rng_tag=rng_tag)
         self.ctx = P.pa_create(D, L, P.PA_PM1, J, None, self.R, betas, n_sweeps, seed, opts)
         self.last_parents = None  # global parents of this shard's copies at the last step
 
@@ -112,6 +112,18 @@ class Shard:
         if self.ctx:
             self.P.pa_destroy(self.ctx)
             self.ctx = None
+
+
+def overlap_histogram(P, shard_a: "Shard", shard_b: "Shard", allreduce=None):
+    """Overlap histogram (Sec. V.A) of two populations split the same way:
+    slot r of population A pairs with slot r of population B, both on the
+    same shard, so each shard counts its own slots and the histograms add
+    (exact integers).  allreduce(h) sums over the shards (None: this shard
+    alone)."""
+    if (shard_a.offset, shard_a.R) != (shard_b.offset, shard_b.R):
+        raise ValueError("the two populations must be split the same way")
+    h = P.pa_overlap(shard_a.ctx, shard_b.ctx)
+    return allreduce(h) if allreduce else h
 
 
 def _serve(gens, requests):

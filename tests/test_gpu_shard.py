@@ -86,3 +86,29 @@ def test_shard_refuses_plain_steps_and_bad_offsets(pa):
     with pytest.raises(P.PAError):
         P.pa_create(3, 4, PM1, J, None, 1000, betas, 2, 5,
                     P.pa_options_default(layout=1, shard_offset=100, shard_total=3000))
+
+
+def test_overlap_of_sharded_populations(pa):
+    """Two populations (tags 0 and 1) split over three shards: the shards'
+    overlap histograms add up to the histogram of the unsplit populations."""
+    P = pa
+    D, L, R, world = 3, 6, 5000, 3
+    J = W.couplings_pm(D, L, 23)
+    betas = W.schedule_lb(6, 3.0)
+    singles = [P.Population(D, L, PM1, J, None, R, betas, 2, 77, layout=P.PA_LAYOUT_PACKED, rng_tag=t)
+               for t in (0, 1)]
+    shards = [[SH.Shard(P, D, L, J, R, betas, 2, 77, s, world, rng_tag=t) for s in range(world)] for t in (0, 1)]
+    try:
+        for _ in range(len(betas)):
+            for pop in singles:
+                assert pop.step()
+            for sh in shards:
+                SH.run_emulated(sh, 1)
+        want = P.pa_overlap(singles[0].ctx, singles[1].ctx)
+        got = sum(SH.overlap_histogram(P, a, b) for a, b in zip(shards[0], shards[1]))
+        np.testing.assert_array_equal(got, want)
+    finally:
+        for pop in singles:
+            pop.close()
+        for sh in shards[0] + shards[1]:
+            sh.close()
