@@ -158,7 +158,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
         else return philox_rk(q, hs, c2, c3, s.rk);
     };
     const int32_t* __restrict__ parent = in.parent;
-    const int ng = min(GPB, G - g0);
+    const int ng = GPB == 1 ? 1 : min(GPB, G - g0);  // g0 < G: one group is always full
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
 
@@ -369,6 +369,14 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
     if (tid < 4) qn[tid] = 0;
     __syncthreads();
     int round = 0;
+    // queue entries are claimed a warp at a time (one shared atomic per 32
+    // entries); lane l takes entry e0 + l, and the loop ends for the whole warp
+    // once a chunk starts past the queue
+    auto claim = [&](int* next) {
+        int e0 = 0;
+        if (lane == 0) e0 = atomicAdd(next, 32);
+        return __shfl_sync(0xffffffffu, e0, 0) + lane;
+    };
     // mode 1 compacts every word with undecided lanes (at low temperature
     // most words have none: L=16 mode-1 steps 14.5 -> 12.0 ms); modes 0 and 2,
     // where most words have undecided lanes, compact only the words still
@@ -417,11 +425,13 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     __syncthreads();
                     const int n = cnt_r[0];
                     if (tid == 0) { qn[2 * ((round + 1) & 1)] = 0; qn[2 * ((round + 1) & 1) + 1] = 0; }
-                    for (int e = atomicAdd(cnt_r + 1, 1); e < n; e = atomicAdd(cnt_r + 1, 1)) {
-                        const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
-                        uint64_t acc2 = 0;
-                        compare_mode1((uint32_t)q2, (uint32_t)(g0 + gl2), hs, QU[e], acc2);
-                        sm[(gl2 * 2 + p) * NH + q2] ^= acc2;
+                    for (int e = claim(cnt_r + 1); e - lane < n; e = claim(cnt_r + 1)) {
+                        if (e < n) {
+                            const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
+                            uint64_t acc2 = 0;
+                            compare_mode1((uint32_t)q2, (uint32_t)(g0 + gl2), hs, QU[e], acc2);
+                            sm[(gl2 * 2 + p) * NH + q2] ^= acc2;
+                        }
                     }
                     __syncthreads();
                 }
@@ -440,8 +450,9 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
             } else {
                 // Late compaction: every word gets its first KLATE Philox calls
                 // in place; a warp then waits for its slowest word only that
-                // far (L=16, k=5..24: 3 calls 2552, 4 calls 2597, 5 calls 2328
-                // attempts/ns).  The words still undecided go to the block queue with
+                // far (L=16, k=5..24, queue claimed a warp at a time: 2 calls
+                // 2293, 3 calls 2666, 4 calls 2714 attempts/ns; 5 calls measured
+                // 2328 with per-thread claims).  The words still undecided go to the block queue with
                 // the class bits of their undecided lanes (those lanes did not
                 // flip, so their classes are unchanged) and finish there on full
                 // warps, one word per thread, without classifying it again.
@@ -479,13 +490,15 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     __syncthreads();
                     const int n = cnt_r[0];
                     if (tid == 0) { qn[2 * ((round + 1) & 1)] = 0; qn[2 * ((round + 1) & 1) + 1] = 0; }
-                    for (int e = atomicAdd(cnt_r + 1, 1); e < n; e = atomicAdd(cnt_r + 1, 1)) {
-                        const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
-                        const uint64_t A = QU[e], Bm = QB[e];
-                        uint64_t U2 = A | Bm, acc2 = 0;
-                        compare_mode02((uint32_t)q2, (uint32_t)(g0 + gl2), hs, U2, A & Bm, Bm & ~A, acc2,
-                                       std::integral_constant<int, KLATE>{}, std::integral_constant<int, 16>{});
-                        sm[(gl2 * 2 + p) * NH + q2] ^= acc2;  // lanes accepted in the queue
+                    for (int e = claim(cnt_r + 1); e - lane < n; e = claim(cnt_r + 1)) {
+                        if (e < n) {
+                            const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
+                            const uint64_t A = QU[e], Bm = QB[e];
+                            uint64_t U2 = A | Bm, acc2 = 0;
+                            compare_mode02((uint32_t)q2, (uint32_t)(g0 + gl2), hs, U2, A & Bm, Bm & ~A, acc2,
+                                           std::integral_constant<int, KLATE>{}, std::integral_constant<int, 16>{});
+                            sm[(gl2 * 2 + p) * NH + q2] ^= acc2;  // lanes accepted in the queue
+                        }
                     }
                     __syncthreads();
                 }
