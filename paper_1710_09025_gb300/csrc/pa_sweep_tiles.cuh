@@ -251,10 +251,14 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
         sw0 = cur[q];
         const uint32_t jm = sj[nb.site];
         uint64_t u[2 * D];
+        // bond signs moved to bit 7 of bytes 0..5 of (ja, jb) by two multiplies
+        // (the shifted copies do not overlap), then replicated over a word by
+        // the sign-replicating byte permute
+        const uint32_t ja = jm * 0x10204080u, jb = jm * 0x408u;
 #pragma unroll
         for (int kk = 0; kk < 2 * D; ++kk) {
-            // coupling sign of bond kk as a 0 / ~0 mask (bit kk sign-extended)
-            const uint32_t m32 = (uint32_t)((int32_t)(jm << (31 - kk)) >> 31);
+            uint32_t m32;
+            asm("prmt.b32 %0, %1, %2, %3;" : "=r"(m32) : "r"(ja), "r"(jb), "r"((uint32_t)(8 | kk) * 0x1111u));
             u[kk] = sw0 ^ oth[nb.q[kk]] ^ (((uint64_t)m32 << 32) | m32);
         }
         if (D == 3) {
@@ -305,8 +309,11 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
         // acts on the undecided lanes U.  L=16, k=5..24 (attempts/ns): one at a
         // time 2713; the first four calls together and then groups of
         // 2 / 3 / 4: 2817 / 2829 / 2797; first calls 3 + 1 or 2 + 2: 2767 / 2776
-        constexpr int kCPI = 4, kCPQ = 3;
-        constexpr int kCP = m0 == 0 ? kCPI : kCPQ;
+        constexpr int kCPI = 4, kCPQ = 3, kCPN = 1;
+        // kCPN: the loop without late compaction (small lattices, the batch:
+        // 512 instances at k=3..12, 1 / 2 / 4 calls side by side: 580.9 /
+        // 578.2 / 565.9 attempts/ns)
+        constexpr int kCP = m1 - m0 == 16 ? kCPN : m0 == 0 ? kCPI : kCPQ;
         auto run_calls = [&](auto step2) {
 #pragma unroll
             for (int m = m0; m < m1; m += kCP) {
