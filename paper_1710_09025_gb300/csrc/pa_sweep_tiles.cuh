@@ -157,6 +157,10 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
         if constexpr (SHARD) return philox_rk_add2(q, hs, c2, c3, s.rk, gadd);
         else return philox_rk(q, hs, c2, c3, s.rk);
     };
+    // (the group index passed to the comparisons is written g0 when a block
+    // holds one group, so that the compiler sees it block-uniform and keeps the
+    // first-round products that depend on it alone off the vector pipes:
+    // L=16, k=5..24: 2837 -> 2875 attempts/ns)
     const int32_t* __restrict__ parent = in.parent;
     const int ng = GPB == 1 ? 1 : min(GPB, G - g0);  // g0 < G: one group is always full
     const int tid = threadIdx.x;
@@ -450,7 +454,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                         if (e < n) {
                             const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
                             uint64_t acc2 = 0;
-                            compare_mode1((uint32_t)q2, (uint32_t)(g0 + gl2), hs, QU[e], acc2);
+                            compare_mode1((uint32_t)q2, (GPB == 1 ? (uint32_t)g0 : (uint32_t)(g0 + gl2)), hs, QU[e], acc2);
                             sm[(gl2 * 2 + p) * NH + q2] ^= acc2;
                         }
                     }
@@ -463,7 +467,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                     uint64_t sw0, b0, b1, b2, down, acc, U;
                     classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
                     start(b0, b1, b2, down, acc, U);
-                    compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
+                    compare_mode02((uint32_t)q, (GPB == 1 ? (uint32_t)g0 : (uint32_t)(g0 + t / NH)), hs, U, b0, b1, acc,
                                    std::integral_constant<int, 0>{}, std::integral_constant<int, 16>{});
                     cur[q] = sw0 ^ acc;
                 }
@@ -493,7 +497,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                             uint64_t sw0, b2, down, acc;
                             classify(t, p, nb_fixed, cur, q, sw0, b0, b1, b2, down);
                             start(b0, b1, b2, down, acc, U);
-                            compare_mode02((uint32_t)q, (uint32_t)(g0 + t / NH), hs, U, b0, b1, acc,
+                            compare_mode02((uint32_t)q, (GPB == 1 ? (uint32_t)g0 : (uint32_t)(g0 + t / NH)), hs, U, b0, b1, acc,
                                            std::integral_constant<int, 0>{}, std::integral_constant<int, KLATE>{});
                             cur[q] = sw0 ^ acc;
                         }
@@ -516,7 +520,7 @@ __device__ __forceinline__ void sweep_packed_tile(const PackedStep& s, const Pac
                             const int t2 = Qt[e], gl2 = t2 / NH, q2 = t2 - gl2 * NH;
                             const uint64_t A = QU[e], Bm = QB[e];
                             uint64_t U2 = A | Bm, acc2 = 0;
-                            compare_mode02((uint32_t)q2, (uint32_t)(g0 + gl2), hs, U2, A & Bm, Bm & ~A, acc2,
+                            compare_mode02((uint32_t)q2, (GPB == 1 ? (uint32_t)g0 : (uint32_t)(g0 + gl2)), hs, U2, A & Bm, Bm & ~A, acc2,
                                            std::integral_constant<int, KLATE>{}, std::integral_constant<int, 16>{});
                             sm[(gl2 * 2 + p) * NH + q2] ^= acc2;  // lanes accepted in the queue
                         }
