@@ -363,9 +363,18 @@ __device__ __forceinline__ void rs_draws_body(const ResampleArgs& a, int q)
         const int k = lo;
         lo = k * seg;
         hi = min(R - 1, k * seg + seg - 1);  // x < P[hi]
-        while (lo < hi) {
-            const int mid = lo + ((hi - lo) >> 1);
-            if (x < rs_P(a, nb, mid)) hi = mid; else lo = mid + 1;
+        if (sb == 1) {
+            // one weights block: x is at least the largest P before it, so
+            // x < max(that, stored P_i) reduces to x < stored P_i
+            while (lo < hi) {
+                const int mid = lo + ((hi - lo) >> 1);
+                if (x < dbits(a.P[mid])) hi = mid; else lo = mid + 1;
+            }
+        } else {
+            while (lo < hi) {
+                const int mid = lo + ((hi - lo) >> 1);
+                if (x < rs_P(a, nb, mid)) hi = mid; else lo = mid + 1;
+            }
         }
     } else {
         // x == S after rounding: the smallest i with P_i >= x
@@ -519,9 +528,9 @@ __device__ __forceinline__ void rs_fill_body(const ResampleArgs& a, int b)
     const int i0 = b * kScanBlock + tid * PER;
     int c[PER];
     int s = 0;
-#pragma unroll
     const int R = rs_src(a);
     const int cap = a.Rdst ? a.cap : 0x7fffffff;
+#pragma unroll
     for (int t = 0; t < PER; ++t) {
         c[t] = (i0 + t < R) ? a.counts[i0 + t] : 0;
         s += c[t];
