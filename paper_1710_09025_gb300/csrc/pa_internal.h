@@ -219,11 +219,16 @@ struct ObsPartial {
     double sumEd, sumE2d, clnc, pad;
 };
 constexpr int kObsBlocks = 608;  // most blocks of the observables reduction (4 per SM of GB300)
-// blocks of the observables reduction for a population of R: about 4096
-// replicas each, at most kObsBlocks (a function of R only)
+// blocks of the observables reduction for a population of R (a function of R
+// only, non-decreasing, so that a grid sized for a capacity covers any smaller
+// population): about 4096 replicas each, but at least min(ceil(R / 1024), 304)
+// blocks, so that small populations spread their FP64 work over many SMs
+// (R = 10^5: 0.048 -> 0.026 ms per step), at most kObsBlocks
 __host__ __device__ constexpr inline int obs_blocks(int R)
 {
-    return R <= 4096 ? 1 : ((R + 4095) / 4096 > kObsBlocks ? kObsBlocks : (R + 4095) / 4096);
+    const int a = (R + 4095) / 4096, b = (R + 1023) / 1024 < 304 ? (R + 1023) / 1024 : 304;
+    const int n = a > b ? a : b;
+    return n < 1 ? 1 : (n > kObsBlocks ? kObsBlocks : n);
 }
 struct ObsArgs {
     int R, kind;
