@@ -73,6 +73,7 @@ struct pa_ctx {
     unsigned long long* hist;
     double *gbar_d, *dJ_d, *dh_d;
     pa::ObsPartial* obspart;
+    double* logc;               // log(c) table of the family entropy
     double* Rk_d;               // populations as doubles (gradient normalisation)
     cudaGraphExec_t gexec;
     std::string err;
@@ -151,7 +152,7 @@ __global__ void acc0_kernel(StepAcc* acc, double betaF0, int R, int* Rdev)
 enum {
     W_J, W_H, W_JNEG, W_JFIX, W_HFIX, W_BETAS, W_S0, W_S1, W_E32, W_E128, W_PARENT, W_FAM0, W_FAM1,
     W_COUNTS, W_BLOCKSUM, W_W, W_P, W_LEV1, W_BMAX, W_UPPER, W_ACC, W_CJ, W_CH, W_TMP8, W_HIST, W_GBAR, W_DJ,
-    W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_WTAB, W_SYNC,
+    W_DH, W_OBSPART, W_RK, W_RDEV, W_ICMERR, W_WTAB, W_SYNC, W_LOGC,
     W_SH_UPPER, W_SH_T2G, W_SH_BMAX, W_SH_POUT, W_SH_FOUT, W_SH_STAGE, W_COUNT
 };
 
@@ -203,6 +204,7 @@ static Layout make_layout(int D, int L, int kind, int layout, int R, int n_temps
     sz[W_DJ] = acc_grad ? sizeof(double) * D * N : 0;
     sz[W_DH] = acc_grad ? sizeof(double) * N : 0;
     sz[W_OBSPART] = sizeof(pa::ObsPartial) * pa::kObsBlocks;
+    sz[W_LOGC] = sizeof(double) * pa::kLogC;
     sz[W_RK] = sizeof(double) * n_temps;
     sz[W_RDEV] = sizeof(int) * n_temps;
     sz[W_ICMERR] = sizeof(int);
@@ -466,6 +468,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
     c->dJ_d = c->acc_grad ? (double*)at(W_DJ) : nullptr;
     c->dh_d = c->acc_grad ? (double*)at(W_DH) : nullptr;
     c->obspart = (pa::ObsPartial*)at(W_OBSPART);
+    c->logc = (double*)at(W_LOGC);
     c->Rk_d = (double*)at(W_RK);
     c->Rdev = (int*)at(W_RDEV);
     c->icm_err = (int*)at(W_ICMERR);
@@ -516,6 +519,7 @@ static int create_impl(pa_ctx** out, int D, int L, int kind, const float* J, con
         if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(StepAcc) * n_temps, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->icm_err, 0, sizeof(int), c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->sync, 0, sizeof(int) * 4, c->st);
+        if (e == cudaSuccess) e = pa::launch_logc_table(c->logc, c->st);
         if (e == cudaSuccess && c->acc_grad) {
             e = cudaMemsetAsync(c->cJ, 0, sizeof(unsigned long long) * (size_t)n_temps * D * N, c->st);
             if (e == cudaSuccess) e = cudaMemsetAsync(c->ch, 0, sizeof(unsigned long long) * (size_t)n_temps * N, c->st);
@@ -765,7 +769,7 @@ static void plan_step(pa_ctx* c, StepPlan* pl)
     pa::ObsArgs& oa = pl->ob;
     oa.R = R; oa.kind = c->kind == PA_PM1 ? 0 : 1; oa.E32 = c->E32; oa.E128 = c->E128;
     if (dyn) { oa.Rdev = c->Rdev + k; oa.R = c->R; }
-    oa.family = c->fam[c->famcur]; oa.part = c->obspart; oa.cur = c->acc + k;
+    oa.family = c->fam[c->famcur]; oa.part = c->obspart; oa.cur = c->acc + k; oa.logc = c->logc;
     oa.sync = c->sync + 2;
     c->k_next = k + 1;
     pl->cur = c->cur;

@@ -237,9 +237,14 @@ struct ObsArgs {
     const longlong2* E128;
     const int32_t* family;
     ObsPartial* part;            // [kObsBlocks] scratch
+    const double* logc;          // [kLogC] log(c) for the family entropy (or null)
     StepAcc* cur;
     int* sync;                   // zeroed block counter: the last block combines (or null)
 };
+// family sizes below kLogC take log(c) from a table that the context fills
+// once with the same device log; larger ones evaluate it
+constexpr int kLogC = 4096;
+cudaError_t launch_logc_table(double* t, cudaStream_t st);
 cudaError_t launch_observe(const ObsArgs& a, cudaStream_t st);
 cudaError_t launch_observe_batched(const ObsArgs* tab, int n_inst, int maxR, cudaStream_t st);
 cudaError_t launch_grad_backward(const unsigned long long* cJ, const unsigned long long* ch,

@@ -642,6 +642,18 @@ cudaError_t launch_resample_batched(const ResampleArgs* tab, int n_inst, int max
     return cudaGetLastError();
 }
 
+// log(c) for c < kLogC (entries 0 and 1 are never read: a run of one adds 0)
+__global__ void logc_table_kernel(double* t)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < kLogC) t[c] = c > 0 ? log((double)c) : 0.0;
+}
+cudaError_t launch_logc_table(double* t, cudaStream_t st)
+{
+    logc_table_kernel<<<(kLogC + 255) / 256, 256, 0, st>>>(t);
+    return cudaGetLastError();
+}
+
 // ---------------- observables (Sec. V.A, Eq. 9; Sec. II.B, Eq. 2) ----------------
 // kObsBlocks blocks each reduce a contiguous slice of the population in a
 // fixed order; one block combines the partials in block order.  The result
@@ -688,10 +700,14 @@ __device__ __forceinline__ void observe_partial_body(const ObsArgs& a)
                 }
                 e = lo;
             }
-            // c ln c of the run; a run of one adds exactly 0 (GB300's FP64 log is costly)
-            if (e - j > 1) {
-                const double c = (double)(e - j);
-                clnc = __fma_rn(c, log(c), clnc);
+            // c ln c of the run; a run of one adds exactly 0 (GB300's FP64 log
+            // is costly: short runs read it from the context's table, which
+            // holds the same device log of the same argument)
+            const int cn = e - j;
+            if (cn > 1) {
+                const double c = (double)cn;
+                const double lc = (a.logc && cn < kLogC) ? a.logc[cn] : log(c);
+                clnc = __fma_rn(c, lc, clnc);
             }
         }
     }
