@@ -82,6 +82,12 @@ def test_fullsize_sampled_parity(pa, oracle, name, checks):
             assert o["E_mean"] == E.astype(np.float64).sum() / R
         fam = P.pa_get_family(pop.ctx)
         assert np.all(np.diff(fam) >= 0)
+        # family entropy S_f = ln R - (1/R) sum_f c_f ln c_f over the downloaded
+        # family ids (runs both shorter and longer than the kernel's log table)
+        _, cnt = np.unique(fam, return_counts=True)
+        c = cnt.astype(np.float64)
+        sf = np.log(R) - np.sum(c * np.log(c)) / R
+        assert o["S_f"] == pytest.approx(sf, rel=1e-10, abs=1e-12)
         assert np.all(np.diff(P.pa_get_parents(pop.ctx)) >= 0)
     finally:
         pop.close()
